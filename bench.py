@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: FSE lost-blocks/s (and Mpix/s, % roofline) on one GB300.
+
+Default workload: one 1024x1024 8-bit image with 20 % of its 8x8 blocks lost
+(bursts + isolated), b=8, B=16, F=64, K=200, tiled by Algorithm 1 into 16
+overlapping tiles (d=32), all tiles in one call.  A step is one full pass of
+the method (tiling, lost-block enumeration and ordering, staging, DFT,
+K iterations, model evaluation, write-back) over that input.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (launched by torch.distributed.run): every rank extrapolates its own
+copy of the workload on its own GPU (replicas; the method's units are
+independent, no data exchange); value = all ranks' blocks / slowest rank.
+"--impl reference" times the FP64 CPU oracle on a bounded sample instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+SMEM_BYTES_PER_CLK_SM = 128  # shared-memory bandwidth per SM per clock
+BYTES_PER_BIN_ITER = 8       # the gathered complex FP32 W(k-u) value
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tiled_1024")
+    ap.add_argument("--mode", default="dag", choices=["dag", "levels", "per_block"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2207_00238_gb300 import synth
+    return synth.CONFIGS[name]()
+
+
+def describe(name, jobs):
+    p = jobs[0]["params"]
+    d = {"workload": name, "images": len(jobs),
+         "size": f"{jobs[0]['image'].shape[1]}x{jobs[0]['image'].shape[0]}" if len(jobs) == 1 else "mixed",
+         "block": p["block"], "border": p["border"], "fft": p["fft"], "K": p["K"],
+         "n_tiles": p["n_tiles"], "overlap": p["overlap"], "order": p["order"],
+         "rho": p["rho"], "delta": p["delta"], "gamma": p["gamma"]}
+    return d
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_blocks_per_s(job, seconds, max_blocks=None):
+    import oracle
+    oracle.build()
+    p = job["params"]
+    kw = dict(block=p["block"], border=p["border"], fft=p["fft"], K=p["K"], rho=p["rho"],
+              delta=p["delta"], gamma=p["gamma"], order=p["order"], n_tiles=p["n_tiles"],
+              overlap=p["overlap"])
+    cores = oracle.threads()
+    if max_blocks is None:
+        probe = max(cores, 4)
+        t = time.perf_counter()
+        r = oracle.fse_image(job["image"], job["mask"], max_blocks=probe, **kw)
+        dt = time.perf_counter() - t
+        per = dt / max(r["stats"]["processed"], 1)
+        max_blocks = max(probe, int(seconds / per))
+    t = time.perf_counter()
+    r = oracle.fse_image(job["image"], job["mask"], max_blocks=max_blocks, **kw)
+    dt = time.perf_counter() - t
+    n = r["stats"]["processed"]
+    return n / dt, n, dt, cores
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    jobs = workload(args.workload)
+    job = jobs[0]
+    per_step = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    _, n, _, cores = oracle_blocks_per_s(job, per_step)
+    for _ in range(args.warmup):
+        oracle_blocks_per_s(job, per_step, max_blocks=n)
+    tot_n, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        _, nn, dt, _ = oracle_blocks_per_s(job, per_step, max_blocks=n)
+        tot_n += nn
+        tot_t += dt
+    value = tot_n / tot_t
+    sample = (f"first {n} lost blocks (processing order, tile 0 first) of the {args.workload} "
+              f"workload per step, FP64 spatial-domain oracle, {cores} threads")
+    line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": describe(args.workload, jobs), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "blocks/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "blocks/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2207_00238_gb300 as fse
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fse.build()
+    jobs = workload(args.workload)
+    dev = torch.device("cuda", local)
+    ctx = fse.Context(local, arena_bytes=4 << 30)
+    ctx.exec_mode(args.mode)
+    keep, cjobs, pix = [], [], 0
+    for j in jobs:
+        img = torch.from_numpy(j["image"]).to(dev)
+        msk = torch.from_numpy(j["mask"]).to(dev)
+        out = torch.empty_like(img)
+        keep += [img, msk, out]
+        cjobs.append(fse.make_job(img, msk, out, j["params"]))
+        pix += img.numel()
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    # one counted pass: blocks per step, bin-iterations per step
+    st = ctx.extrapolate(cjobs, stream=sptr, stats=True)
+    blocks, core_blocks, bins = st["lost_blocks"], st["core_lost_blocks"], st["bin_iterations"]
+    launches_per_step = st["launches"]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        ctx.extrapolate(cjobs, stream=sptr, stats=False)
+    ctx.set_option(fse.OPT_KERNEL_TIMING, 1)
+    ctx.kernel_times()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                    if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.fill_(float(i))  # evict the inputs from L2 between steps
+        starts[i].record(stream)
+        ctx.extrapolate(cjobs, stream=sptr, stats=False)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms = ctx.kernel_times()
+    ctx.set_option(fse.OPT_KERNEL_TIMING, 0)
+    total_s = sum(step_ms) / 1000.0
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * blocks * args.steps / total_s
+    mpix = world * pix * args.steps / total_s / 1e6
+
+    # roofline of the dominant kernel (the iteration loop): algorithmic shared-
+    # memory bytes (8 B of W per bin-iteration) / its event-timed duration
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gbs = SMEM_BYTES_PER_CLK_SM * sms * f_max * 1e6 / 1e9
+    kmean = statistics.mean(kern_ms) if kern_ms else float("nan")
+    achieved = bins * BYTES_PER_BIN_ITER / (kmean / 1000.0) / 1e9
+    roof = {"bound": "alu", "pipe": "shared-memory (LSU) pipe, 128 B/clk/SM",
+            "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
+            "traffic": None, "kernel": "k_exec_f32_64" if jobs[0]["params"]["fft"] == 64 else "k_exec_f32_32",
+            "kernel_ms": kmean, "bin_iterations_per_launch": bins,
+            "peak_basis": f"derived: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {sms} SMs x {f_max:.0f} MHz"}
+    if clk:
+        roof["frac_at_observed_clock"] = achieved / (SMEM_BYTES_PER_CLK_SM * sms * clk["sm_mhz"] * 1e6 / 1e9)
+
+    # end to end through the host-buffer entry point (copies timed)
+    e2e = None
+    if not args.no_e2e:
+        hj, hkeep = [], []
+        for j in jobs:
+            himg = torch.from_numpy(j["image"]).pin_memory()
+            hmsk = torch.from_numpy(j["mask"]).pin_memory()
+            hout = torch.empty_like(himg).pin_memory()
+            hkeep += [himg, hmsk, hout]
+            hj.append(fse.make_job(himg.numpy(), hmsk.numpy(), hout.numpy(), j["params"]))
+        e2e_ctx = fse.Context(local, arena_bytes=4 << 30)
+        for _ in range(args.warmup):
+            e2e_ctx.extrapolate_host(hj, stream=sptr)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            e2e_ctx.extrapolate_host(hj, stream=sptr)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * blocks * args.steps / e2e_s, "unit": "blocks/s",
+               "h2d_bytes_per_step": 2 * pix, "d2h_bytes_per_step": pix,
+               "mpix_per_s": world * pix * args.steps / e2e_s / 1e6}
+        e2e_ctx.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, n, dt, cores = oracle_blocks_per_s(jobs[0], args.cpu_seconds)
+        cpu = {"value": v, "unit": "blocks/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {n} lost blocks (processing order, tile 0 first) of the "
+                         f"{args.workload} workload, {dt:.1f} s, FP64 spatial-domain projections"}
+    if rank == 0:
+        cfg = describe(args.workload, jobs)
+        cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                    "exec_mode": args.mode, "l2": "flushed between steps (512 MB write)",
+                    "lost_blocks_per_step": blocks, "core_lost_blocks_per_step": core_blocks,
+                    "bin_iterations_per_step": bins})
+        line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": cfg, "mpix_per_s": mpix, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * fse.h -- C ABI of a single-GPU (sm_103a) library for Frequency Selective
+ * Extrapolation (FSE) on the overlapping tiles of Seiler & Kaup's tiling
+ * algorithm ("Distributed Parallel Image Signal Extrapolation Framework using
+ * Message Passing Interface").
+ *
+ * Method (paper Sec. II and Sec. III):
+ *   - The image is cut into N compact tiles by Algorithm 1 (Eqs. 1-5); each
+ *     tile is grown by a stripe of d pixels on every side and extrapolated as
+ *     a standalone image; the cores are merged into the output.
+ *   - Inside a tile, every b x b block holding a lost pixel is modelled from
+ *     its (b+2B) x (b+2B) support as a sparse sum of F x F Fourier basis
+ *     functions, chosen greedily over K iterations (Sec. II): weights
+ *     rho^dist on known pixels, delta*rho^dist on pixels reconstructed by
+ *     earlier blocks, 0 on still-lost pixels; per iteration the bin u with
+ *     the largest weighted residual energy |R_w(u)|^2 is picked, its
+ *     coefficient grows by gamma*R_w(u)/W(0), and the shifted weight spectrum
+ *     gamma*R_w(u)/W(0) * W(k-u) is subtracted from R_w; the model's real part
+ *     fills the block's lost pixels.
+ *
+ * Conventions for every call:
+ *   - Return value: FSE_OK (0) or a negative FSE_E* status.  No call aborts,
+ *     traps or exits the process.  fse_last_error() gives a thread-local text.
+ *   - Images are 8-bit, row-major with a row pitch in bytes; mask != 0 marks a
+ *     lost pixel.  Known pixels are copied to the output unchanged.
+ *   - "Device pointer" means memory of the context's GPU (cudaMalloc, or a
+ *     torch tensor's data_ptr()); "host pointer" means ordinary or pinned
+ *     host memory.  The caller keeps ownership of every buffer it passes.
+ *   - Handles are created and destroyed only by the library.
+ */
+#ifndef FSE_H
+#define FSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FSE_OK 0
+#define FSE_EINVAL (-1)      /* bad argument or parameter                     */
+#define FSE_EDEGENERATE (-2) /* Algorithm 1 produced a tile with w<=0 or h<=0 */
+#define FSE_ENOMEM (-3)      /* arena or host allocation too small            */
+#define FSE_EBUSY (-4)       /* server queue full                             */
+#define FSE_ETIMEOUT (-5)    /* a bounded device or host wait ran out         */
+#define FSE_ECUDA (-6)       /* a CUDA runtime call failed                    */
+#define FSE_ENOTFOUND (-7)   /* unknown server ticket                         */
+#define FSE_ECANCELLED (-8)  /* request cancelled or server shut down         */
+
+/* ---- processing order of the lost blocks inside one tile ----------------
+ * The paper defers the order to an earlier FSE publication (Sec. II) and
+ * does not define it; these are the library's readings.
+ *   PHASED      : P = ceil(B/b)+1; blocks sorted by ((I mod P)*P + J mod P, I, J).
+ *                 Two blocks of one phase never lie in each other's support,
+ *                 so a phase runs in parallel with sequential semantics.
+ *   RASTER      : blocks sorted by (I, J).
+ *   INDEPENDENT : no block ever uses another block's reconstruction. */
+#define FSE_ORDER_PHASED 0
+#define FSE_ORDER_RASTER 1
+#define FSE_ORDER_INDEPENDENT 2
+
+/* ---- tiling (Algorithm 1, Eqs. 1-5; overlap stripe of Sec. III) ---------- */
+typedef struct fse_tile_t {
+    int32_t x, y, w, h;     /* core tile: offset and size (Algorithm 1)      */
+    int32_t ex, ey, ew, eh; /* core grown by d on each side, clipped to image */
+} fse_tile_t;
+
+/*
+ * fse_plan_tiles -- Algorithm 1 with the overlap stripe d.  Host only, pure,
+ * thread-safe.
+ *   W, H  : image width and height (> 0).  W < H is tiled with the axes
+ *           swapped and swapped back ("landscape assumed", Sec. III).
+ *   N     : number of tiles (> 0);  d : overlap stripe width (>= 0).
+ *   out   : caller-owned array of cap entries; tiles come row by row.
+ *   n_out : receives N on success.
+ * Eq. (2) rounds half up, evaluated in exact integers.
+ * Errors: FSE_EINVAL (non-positive sizes, d < 0, cap < N, NULL out),
+ *         FSE_EDEGENERATE (a tile of width or height <= 0, e.g. 32x32, N=23).
+ */
+int fse_plan_tiles(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out, int32_t cap,
+                   int32_t* n_out);
+
+/* ---- parameters of one extrapolation job -------------------------------- */
+typedef struct fse_params_t {
+    int32_t block;  /* b: block size (1..16)                                 */
+    int32_t border; /* B: support border; support S = b + 2B                 */
+    int32_t fft;    /* F: DFT size per axis, 32 or 64, F >= S                */
+    int32_t K;      /* iterations (0..256)                                   */
+    double rho;     /* weight decay, 0 < rho <= 1                            */
+    double delta;   /* weight factor of reconstructed pixels, >= 0           */
+    double gamma;   /* coefficient step, 0 < gamma < 2                       */
+    int32_t order;  /* FSE_ORDER_*                                           */
+    int32_t n_tiles;   /* N of Algorithm 1 (>= 1)                            */
+    int32_t overlap;   /* d (>= 0)                                           */
+    int32_t precision; /* 32: FP32 fast path; 64: FP64 validation path       */
+} fse_params_t;
+
+typedef struct fse_job_t {
+    const uint8_t* image; /* W x H, row pitch `pitch` bytes                   */
+    const uint8_t* mask;  /* same layout; != 0 marks a lost pixel             */
+    uint8_t* out;         /* same layout; receives the extrapolated image     */
+    float* out_f32;       /* optional (NULL): W x H floats, row stride W; the
+                             unrounded model at lost pixels, the input elsewhere */
+    double* out_f64;      /* optional (NULL): as out_f32 in FP64 (exact model
+                             values of the FP64 validation path)               */
+    int32_t W, H, pitch;
+    fse_params_t p;
+} fse_job_t;
+
+typedef struct fse_stats_t {
+    int64_t lost_blocks;      /* block runs, overlap duplicates included     */
+    int64_t core_lost_blocks; /* lost blocks counted once per image           */
+    int64_t empty_blocks;     /* blocks whose support had sum(w) == 0        */
+    int64_t pixels;           /* input pixels, sum of W*H                     */
+    int64_t bin_iterations;   /* sum over modelled blocks of K*F*F            */
+    int32_t jobs, tiles, launches, graph_replayed;
+    float device_ms;          /* stream time of the whole call (events)       */
+    float exec_ms;            /* stream time of the iteration kernels         */
+} fse_stats_t;
+
+/* ---- context: one GPU, one device arena ---------------------------------- */
+typedef struct fse_context fse_context_t;
+
+/*
+ * fse_context_create -- binds the calling thread's work to `device`, reserves
+ * `arena_bytes` of device memory (cudaMalloc, once) for all per-call state and
+ * reads the autotuner cache `tune_cache_path` (may be NULL; a missing file is
+ * not an error).  Errors: FSE_EINVAL, FSE_ENOMEM, FSE_ECUDA.
+ */
+int fse_context_create(fse_context_t** ctx, int device, size_t arena_bytes,
+                       const char* tune_cache_path);
+void fse_context_destroy(fse_context_t* ctx);
+
+/* Options (fse_context_set_option). */
+#define FSE_OPT_EXEC_MODE 1     /* FSE_EXEC_*                                  */
+#define FSE_OPT_TIMEOUT_MS 2    /* bound of every device wait (default 20000)  */
+#define FSE_OPT_CTAS_PER_SM 3   /* 0 = autotuned / occupancy-derived          */
+#define FSE_OPT_USE_GRAPH 4     /* 1 = capture each batch in a CUDA graph and
+                                   replay it while the job set is unchanged    */
+#define FSE_OPT_DEBUG_CAPTURE 5 /* 1 = record each block's selected bins       */
+#define FSE_OPT_KERNEL_TIMING 6 /* 1 = bracket the iteration kernels of every
+                                   call with CUDA events (no synchronisation);
+                                   read with fse_context_kernel_times         */
+#define FSE_EXEC_DAG 0       /* one persistent launch per DFT class; blocks start
+                                as soon as the blocks they depend on are done  */
+#define FSE_EXEC_LEVELS 1    /* one launch per order level (phase)            */
+#define FSE_EXEC_PER_BLOCK 2 /* one launch per lost block, in processing order */
+int fse_context_set_option(fse_context_t* ctx, int32_t key, int64_t value);
+
+/*
+ * fse_context_kernel_times -- with FSE_OPT_KERNEL_TIMING = 1: synchronises the
+ * context's GPU, writes the elapsed milliseconds of the iteration kernels of
+ * each call since the option was set (oldest first, at most cap) and forgets
+ * them.  Returns the count written.
+ */
+int32_t fse_context_kernel_times(fse_context_t* ctx, float* ms, int32_t cap);
+
+/*
+ * fse_extrapolate_batch -- extrapolates n jobs in one stream-ordered pass.
+ *   jobs[i].image/mask/out/out_f32 are DEVICE pointers on the context's GPU,
+ *   valid until the work on `cuda_stream` (a cudaStream_t; NULL = default
+ *   stream) completes.  All tiles of all jobs share the launches.
+ *   stats (may be NULL): when non-NULL the call synchronises the stream and
+ *   fills it; when NULL the call returns without waiting.
+ * Device state lives in the context's arena only; no other allocation.
+ * Errors: FSE_EINVAL (a bad job or parameter; nothing is launched),
+ *         FSE_EDEGENERATE, FSE_ENOMEM (arena too small), FSE_ETIMEOUT (a device
+ *         wait ran out; outputs undefined), FSE_ECUDA.
+ */
+int fse_extrapolate_batch(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void* cuda_stream,
+                          fse_stats_t* stats);
+
+/*
+ * fse_extrapolate_host -- as fse_extrapolate_batch, but image/mask/out/out_f32
+ * are HOST pointers: inputs are copied to the arena, outputs copied back, and
+ * the call returns after the copies finished.  Pinned host memory makes the
+ * copies asynchronous DMA.
+ */
+int fse_extrapolate_host(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void* cuda_stream,
+                         fse_stats_t* stats);
+
+/* ---- serving: continuous batching ---------------------------------------- */
+typedef struct fse_server fse_server_t;
+typedef struct fse_server_cfg_t {
+    size_t arena_bytes;    /* device bytes for resident request state        */
+    int32_t max_queue;     /* pending requests before FSE_EBUSY              */
+    int32_t max_resident;  /* requests resident on the GPU at once           */
+    int32_t tick_items;    /* block budget per device tick (0 = automatic)   */
+} fse_server_cfg_t;
+
+#define FSE_REQ_QUEUED 0
+#define FSE_REQ_RUNNING 1
+#define FSE_REQ_DONE 2
+#define FSE_REQ_FAILED 3
+
+/*
+ * fse_server_create -- starts the serving thread on the context's GPU.  The
+ * server owns its own device memory (cfg->arena_bytes); the context's arena is
+ * not used.  Requests are admitted while their estimated device bytes fit
+ * the free memory, their image and mask stay resident until done, and blocks
+ * of every resident request share each device tick.
+ */
+int fse_server_create(fse_server_t** srv, fse_context_t* ctx, const fse_server_cfg_t* cfg);
+/*
+ * fse_submit -- queues one job; image/mask/out/out_f32 are HOST pointers.
+ * image and mask are copied before the call returns; out (and out_f32) must
+ * stay valid until fse_wait returns for this ticket.  FSE_EBUSY when full.
+ */
+int fse_submit(fse_server_t* srv, const fse_job_t* job, uint64_t* ticket);
+int fse_poll(fse_server_t* srv, uint64_t ticket, int32_t* state);
+/* Waits up to timeout_ms (< 0: no limit) for completion; st may be NULL.
+ * Returns FSE_OK, the request's error status, FSE_ETIMEOUT or FSE_ENOTFOUND.
+ * A completed ticket is forgotten after fse_wait returns FSE_OK for it. */
+int fse_wait(fse_server_t* srv, uint64_t ticket, int32_t timeout_ms, fse_stats_t* st);
+/* Per-request latency record of the last completed tickets (seconds from
+ * submit to done), newest last; returns how many were written. */
+int32_t fse_server_latencies(fse_server_t* srv, double* out, int32_t cap);
+void fse_server_destroy(fse_server_t* srv);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+const char* fse_last_error(void);
+
+/*
+ * fse_debug_fetch -- after a batch run with FSE_OPT_DEBUG_CAPTURE = 1, copies
+ * out one record per processed block: rec[4*i..] = job, tile, I, J (block row
+ * and column in the tile-local grid) and useq[K_max*i..] = the selected bins
+ * (flat k1*F+k2) of its iterations, -1 past its K.  Returns the record count
+ * (or a negative status).  K_max is the largest K of the batch.
+ */
+int32_t fse_debug_fetch(fse_context_t* ctx, int32_t* rec, int32_t* useq, int32_t cap,
+                        int32_t* K_max);
+
+/*
+ * fse_debug_wait_probe -- launches the work-queue consumer on an empty queue
+ * whose producer never comes, with the given wait bound.  Returns
+ * FSE_ETIMEOUT when the bounded wait ran out as designed (the context stays
+ * usable), another status otherwise.  Exercises the failure path without
+ * any device fault.
+ */
+int fse_debug_wait_probe(fse_context_t* ctx, int32_t timeout_us);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSE_H */

@@ -363,6 +363,7 @@ int oracle_fse_image(const uint8_t *img, const uint8_t *mask, int32_t W, int32_t
             int32_t *gstat = malloc(sizeof(int32_t) * ng);
             double *gw0 = malloc(sizeof(double) * ng);
             int32_t *gseq = malloc(sizeof(int32_t) * (size_t)ng * (K > 0 ? K : 1));
+            memset(gseq, 0xFF, sizeof(int32_t) * (size_t)ng * (K > 0 ? K : 1)); /* -1: not iterated */
 
 #pragma omp parallel for schedule(dynamic)
             for (int q = 0; q < ng; q++) {

@@ -1,0 +1,209 @@
+// extern "C" entry points declared in include/fse.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fse.h"
+#include "fse_context.h"
+#include "fse_internal.h"
+
+using fse::Context;
+
+namespace fse {
+
+// Autotuner cache: one line per work class, "cls ctas_per_sm", keyed by the
+// GPU name on the first line.  A missing or foreign file is ignored.
+void tune_load(Context* c) {
+  FILE* f = fopen(c->tune_path.c_str(), "r");
+  if (!f) return;
+  char name[256] = {0};
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, c->device);
+  if (fgets(name, sizeof(name), f)) {
+    name[strcspn(name, "\r\n")] = 0;
+    if (strcmp(name, prop.name) == 0) {
+      int k, v;
+      while (fscanf(f, "%d %d", &k, &v) == 2)
+        if (k >= 0 && k < MAX_CLS && v > 0) c->tuned_ctas[k] = v;
+    }
+  }
+  fclose(f);
+}
+
+}  // namespace fse
+
+extern "C" {
+
+int fse_plan_tiles(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out, int32_t cap,
+                   int32_t* n_out) {
+  return fse::plan_tiles(W, H, N, d, out, cap, n_out);
+}
+
+int fse_context_create(fse_context_t** ctx, int device, size_t arena_bytes,
+                       const char* tune_cache_path) {
+  if (!ctx) return fse::fail(FSE_EINVAL, "NULL ctx");
+  return fse::context_create(ctx, device, arena_bytes, tune_cache_path);
+}
+
+void fse_context_destroy(fse_context_t* ctx) { fse::context_destroy(ctx); }
+
+int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
+  if (!c) return fse::fail(FSE_EINVAL, "NULL ctx");
+  switch (key) {
+    case FSE_OPT_EXEC_MODE:
+      if (value < FSE_EXEC_DAG || value > FSE_EXEC_PER_BLOCK) return fse::fail(FSE_EINVAL, "exec mode");
+      c->exec_mode = (int)value;
+      return FSE_OK;
+    case FSE_OPT_TIMEOUT_MS:
+      if (value < 1 || value > 3600 * 1000) return fse::fail(FSE_EINVAL, "timeout_ms");
+      c->timeout_ms = (int)value;
+      return FSE_OK;
+    case FSE_OPT_CTAS_PER_SM:
+      if (value < 0 || value > 64) return fse::fail(FSE_EINVAL, "ctas_per_sm");
+      c->ctas_per_sm = (int)value;
+      return FSE_OK;
+    case FSE_OPT_USE_GRAPH:
+      c->use_graph = value != 0;
+      return FSE_OK;
+    case FSE_OPT_DEBUG_CAPTURE:
+      c->debug = value != 0;
+      return FSE_OK;
+    case FSE_OPT_KERNEL_TIMING:
+      c->kernel_timing = value != 0;
+      c->tev_used = 0;
+      return FSE_OK;
+    default:
+      return fse::fail(FSE_EINVAL, "unknown option %d", key);
+  }
+}
+
+int fse_extrapolate_batch(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void* cuda_stream,
+                          fse_stats_t* stats) {
+  return fse::run_batch(ctx, jobs, n, (cudaStream_t)cuda_stream, stats, 0);
+}
+
+int fse_extrapolate_host(fse_context_t* c, const fse_job_t* jobs, int32_t n, void* cuda_stream,
+                         fse_stats_t* stats) {
+  if (!c) return fse::fail(FSE_EINVAL, "NULL ctx");
+  if (n < 0 || (n > 0 && !jobs)) return fse::fail(FSE_EINVAL, "bad job list");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fse::fail(FSE_ECUDA, "cudaSetDevice");
+  // device copies of image, mask, out (pitch W) and out_f32 at the arena front
+  std::vector<fse_job_t> dj(jobs, jobs + n);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = (off + 255) / 256 * 256; off = r + bytes; return r; };
+  for (int i = 0; i < n; ++i) {
+    int rc = fse::check_job(jobs[i], i);
+    if (rc) return rc;
+    const size_t px = (size_t)jobs[i].W * jobs[i].H;
+    dj[i].image = (const uint8_t*)(c->arena + take(px));
+    dj[i].mask = (const uint8_t*)(c->arena + take(px));
+    dj[i].out = (uint8_t*)(c->arena + take(px));
+    dj[i].out_f32 = jobs[i].out_f32 ? (float*)(c->arena + take(px * 4)) : nullptr;
+    dj[i].out_f64 = jobs[i].out_f64 ? (double*)(c->arena + take(px * 8)) : nullptr;
+    dj[i].pitch = jobs[i].W;
+  }
+  off = (off + 255) / 256 * 256;
+  if (off >= c->arena_bytes) return fse::fail(FSE_ENOMEM, "arena too small for the host path");
+  for (int i = 0; i < n; ++i) {
+    const fse_job_t& j = jobs[i];
+    cudaError_t e = cudaMemcpy2DAsync((void*)dj[i].image, j.W, j.image, j.pitch, j.W, j.H,
+                                      cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync((void*)dj[i].mask, j.W, j.mask, j.pitch, j.W, j.H,
+                            cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fse::cuda_fail(e, "host-to-device copy");
+  }
+  int rc = fse::run_batch(c, dj.data(), n, st, stats, off);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    const fse_job_t& j = jobs[i];
+    cudaError_t e = cudaMemcpy2DAsync(j.out, j.pitch, dj[i].out, j.W, j.W, j.H,
+                                      cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && j.out_f32)
+      e = cudaMemcpyAsync(j.out_f32, dj[i].out_f32, sizeof(float) * j.W * j.H,
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && j.out_f64)
+      e = cudaMemcpyAsync(j.out_f64, dj[i].out_f64, sizeof(double) * j.W * j.H,
+                          cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fse::cuda_fail(e, "device-to-host copy");
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fse::cuda_fail(e, "cudaStreamSynchronize");
+  return FSE_OK;
+}
+
+const char* fse_last_error(void) { return fse::last_error(); }
+
+int32_t fse_context_kernel_times(fse_context_t* c, float* ms, int32_t cap) {
+  if (!c || (!ms && cap > 0)) return fse::fail(FSE_EINVAL, "NULL argument");
+  if (cudaSetDevice(c->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return fse::fail(FSE_ECUDA, "synchronize");
+  int32_t n = 0;
+  for (size_t i = 0; i + 1 < c->tev_used && n < cap; i += 2) {
+    float v = 0;
+    if (cudaEventElapsedTime(&v, c->tev[i], c->tev[i + 1]) != cudaSuccess)
+      return fse::fail(FSE_ECUDA, "cudaEventElapsedTime");
+    ms[n++] = v;
+  }
+  c->tev_used = 0;
+  return n;
+}
+
+int32_t fse_debug_fetch(fse_context_t* c, int32_t* rec, int32_t* useq, int32_t cap,
+                        int32_t* K_max) {
+  if (!c || !rec || !useq || !K_max) return fse::fail(FSE_EINVAL, "NULL argument");
+  if (!c->last_dbg_rec) return fse::fail(FSE_EINVAL, "no captured batch (FSE_OPT_DEBUG_CAPTURE)");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fse::fail(FSE_ECUDA, "cudaSetDevice");
+  if (cudaDeviceSynchronize() != cudaSuccess) return fse::fail(FSE_ECUDA, "sync");
+  const size_t n = (size_t)fse::MAX_CLS * c->last_dbg_cap;
+  std::vector<int32_t> r(n * 4), u(n * fse::KMAX);
+  if (cudaMemcpy(r.data(), c->last_dbg_rec, r.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(u.data(), c->last_dbg_useq, u.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fse::fail(FSE_ECUDA, "debug copy");
+  const int K = c->last_K_max;
+  *K_max = K;
+  int32_t m = 0;
+  for (size_t i = 0; i < n && m < cap; ++i) {
+    if (r[i * 4] < 0) continue;
+    memcpy(rec + 4 * m, &r[i * 4], 16);
+    for (int k = 0; k < K; ++k) useq[(size_t)m * K + k] = u[i * fse::KMAX + k];
+    ++m;
+  }
+  return m;
+}
+
+int fse_debug_wait_probe(fse_context_t* c, int32_t timeout_us) {
+  if (!c || timeout_us <= 0) return fse::fail(FSE_EINVAL, "bad arguments");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fse::fail(FSE_ECUDA, "cudaSetDevice");
+  // a queue with one item whose producer never runs
+  fse::QueueDev* q = reinterpret_cast<fse::QueueDev*>(c->arena);
+  int32_t* slots = reinterpret_cast<int32_t*>(c->arena + 256);
+  fse::QueueDev hq;
+  memset(&hq, 0, sizeof(hq));
+  hq.n_items = 1;
+  if (cudaMemcpy(q, &hq, sizeof(hq), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(slots, 0xFF, 4) != cudaSuccess)
+    return fse::fail(FSE_ECUDA, "probe setup");
+  fse::ExecArgs a;
+  memset(&a, 0, sizeof(a));
+  a.c[0].q = q;
+  a.c[0].slots = slots;
+  a.c[0].cap = 1;
+  a.single_item = -1;
+  a.timeout_ns = (int64_t)timeout_us * 1000;
+  cudaError_t e = fse::launch_probe(a, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fse::cuda_fail(e, "probe");
+  if (cudaMemcpy(&hq, q, sizeof(hq), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fse::fail(FSE_ECUDA, "probe readback");
+  c->graph_jobs.clear();  // the arena front was overwritten
+  if (hq.error & fse::ERR_TIMEOUT) return fse::fail(FSE_ETIMEOUT, "wait ran out after %d us", timeout_us);
+  return FSE_OK;
+}
+
+}  // extern "C"

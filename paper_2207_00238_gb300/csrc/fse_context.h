@@ -1,0 +1,61 @@
+// Context state behind the opaque fse_context_t handle.
+#pragma once
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fse.h"
+#include "fse_internal.h"
+
+struct fse_context {
+  int device = 0;
+  int sm_count = 0;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  char* host_buf = nullptr;  // pinned staging of the per-call tables
+  size_t host_cap = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  // options
+  int exec_mode = FSE_EXEC_DAG;
+  int timeout_ms = 20000;
+  int ctas_per_sm = 0;
+  int use_graph = 0;
+  int debug = 0;
+  int kernel_timing = 0;
+  int capturing = 0;
+  std::vector<cudaEvent_t> tev;  // pairs: start, end of the iteration kernels
+  size_t tev_used = 0;
+  int occupancy[fse::MAX_CLS] = {1, 1, 1};
+  std::string tune_path;
+  int tuned_ctas[fse::MAX_CLS] = {0, 0, 0};
+  // cached graph of the last job set
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<fse_job_t> graph_jobs;
+  int graph_mode = -1, graph_debug = -1, graph_launches = 0;
+  // last call (for fse_debug_fetch / fse_context_check)
+  int64_t last_cap[fse::MAX_CLS] = {0, 0, 0};
+  fse::QueueDev* last_q = nullptr;
+  int32_t* last_dbg_rec = nullptr;
+  int32_t* last_dbg_useq = nullptr;
+  int32_t last_dbg_cap = 0;
+  int32_t last_K_max = 0;
+};
+
+namespace fse {
+using Context = fse_context;
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+int plan_tiles(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out, int32_t cap,
+               int32_t* n_out);
+int check_job(const fse_job_t& j, int idx);
+int context_create(Context** out, int device, size_t arena_bytes, const char* tune_path);
+void context_destroy(Context* c);
+int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse_stats_t* stats,
+              size_t arena_offset);
+int exec_grid(Context* c, int cls);
+void tune_load(Context* c);
+const char* last_error();
+}  // namespace fse

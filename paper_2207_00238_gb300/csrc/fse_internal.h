@@ -1,0 +1,106 @@
+// Internal layout shared by the host executor (fse_api.cpp) and the kernels
+// (fse_kernels.cu).  Plain structs only; every pointer is a device address.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace fse {
+
+constexpr int KMAX = 256;       // iterations per block (coefficient list in smem)
+constexpr int BMAX = 16;        // largest block size
+constexpr int MAX_CLS = 3;      // work classes, one executor kernel each
+constexpr double TAU_F64 = 1e-9;  // FP64 tie tolerance of the argmax
+
+// Work classes: which executor kernel runs a job's blocks.
+enum Cls : int32_t {
+  CLS_F32_32 = 0,  // FP32, F = 32: one warp per block, spectrum in registers
+  CLS_F32_64 = 1,  // FP32, F = 64: four warps per block
+  CLS_F64 = 2,     // FP64 validation path, F = 32 or 64
+};
+
+enum Order : int32_t { ORDER_PHASED = 0, ORDER_RASTER = 1, ORDER_INDEPENDENT = 2 };
+
+enum ErrBits : int32_t { ERR_TIMEOUT = 1, ERR_BOUNDS = 2 };
+
+struct JobDev {
+  const uint8_t* image;
+  const uint8_t* mask;
+  uint8_t* out;
+  float* out_f32;  // may be null
+  double* out_f64; // may be null
+  int32_t W, H, pitch;
+  int32_t b, B, S, F, K, order, P, D, cls;
+  float rho_f, delta_f, gamma_f;
+  double rho, delta, gamma;
+  const float* wiso_f;   // S*S, rho^dist about the block centre
+  const double* wiso_d;  // same in FP64
+};
+
+struct TileDev {
+  int32_t job;
+  int32_t x, y, w, h;      // core
+  int32_t ex, ey, ew, eh;  // extended
+  int32_t nbx, nby;        // tile-local block grid
+  int32_t cls;
+  int64_t map_off;  // first block of this tile in the block map
+  int64_t val_off;  // first pixel of this tile's value plane (elements)
+};
+
+// Per-class work queue: items become ready when every block they depend on
+// is done; consumers pop slots in order and wait (bounded) for the slot's
+// producer.
+struct QueueDev {
+  int32_t n_items;  // items of this class (written by the planner)
+  int32_t head;     // next slot to pop
+  int32_t tail;     // next slot to push
+  int32_t n_done;
+  int32_t n_empty;
+  int32_t n_core;   // lost blocks that touch their tile's core
+  int32_t error;    // ErrBits
+  int32_t error_info;
+};
+
+struct ClassArgs {
+  int2* items;      // (tile, I << 16 | J)
+  int32_t* cnt;     // unfinished predecessors per item
+  int32_t* slots;   // ready queue, -1 = not yet pushed
+  QueueDev* q;
+  int32_t cap;
+};
+
+struct ExecArgs {
+  const JobDev* jobs;
+  const TileDev* tiles;
+  int32_t* map;  // per tile block: item id within its class, -1 if not lost
+  float* val_f;  // value planes of FP32 jobs (NaN = pending)
+  double* val_d; // value planes of FP64 jobs
+  ClassArgs c[MAX_CLS];
+  int64_t timeout_ns;
+  // optional per-item capture of the selected bins
+  int32_t* dbg_rec;   // 4 per item and class: job, tile, I, J
+  int32_t* dbg_useq;  // KMAX per item
+  int32_t dbg_cap;
+  // level-synchronous / per-block execution: only items of this level key
+  int32_t level_mode;   // 0 = DAG, 1 = only items whose level == level
+  int32_t level;
+  int32_t single_item;  // >= 0: process exactly this item (per-block launch)
+  int32_t* level_of;    // per class item level (levels mode), class stride level_stride
+  int64_t level_stride;
+};
+
+// Launch wrappers (fse_kernels.cu).  All are stream-ordered, none syncs.
+void set_twiddles(const float2* tw_f, const double2* tw_d);  // 64 entries each
+cudaError_t launch_init_out(const JobDev* jobs_dev, int n_jobs, int max_pixels,
+                            cudaStream_t st);
+cudaError_t launch_mark(const ExecArgs& a, int n_tiles, int max_tile_blocks, cudaStream_t st);
+cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st);
+cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st);
+cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st);
+int exec_threads(int cls);
+size_t exec_smem(int cls);
+cudaError_t exec_setup(int device);  // smem opt-in for every executor kernel
+const void* exec_kernel_ptr(int cls);
+
+}  // namespace fse

@@ -1,0 +1,970 @@
+// FSE device kernels for sm_103a.
+//
+// Per lost block (paper Sec. II; the method's steps in order):
+//   stage   : gather the S x S support (S = b + 2B) around the block from the
+//             8-bit image, the loss mask and the tile's value plane; weight
+//             w = rho^dist (known), delta*rho^dist (reconstructed), 0 (pending
+//             or outside the extended tile); z = w + i*w*r.
+//   DFT     : one packed complex F x F FFT of z (zero padded S -> F), split by
+//             Hermitian symmetry into W = DFT(w) and R_w = DFT(w*r).
+//   iterate : K times: u = argmax_k |R_w(k)|^2; Delta = gamma R_w(u) / W(0);
+//             record (u, Delta); R_w(k) -= Delta * W(k - u) for every bin k.
+//   model   : g = Re sum Delta_nu exp(+2 pi i u_nu . x / F) at the block's
+//             pending pixels; store g in the tile's value plane (now
+//             "reconstructed"), write round-half-even(clip(g)) to the output
+//             if the pixel lies in the tile's core (crop and merge, Sec. III).
+//   release : blocks whose support holds this block and that come later in the
+//             processing order lose one pending predecessor; at zero they are
+//             queued.
+//
+// Work distribution: every lost block of every extended tile of every job is
+// one work item; one persistent launch per work class drains a ready queue.
+// Waits on the queue are bounded by a wall-clock limit (globaltimer) and end
+// with an error flag that the host reads; nothing traps.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fse_internal.h"
+
+namespace fse {
+
+__constant__ float2 c_twf[64];   // exp(-2 pi i q / 64)
+__constant__ double2 c_twd[64];
+
+void set_twiddles(const float2* tw_f, const double2* tw_d) {
+  cudaMemcpyToSymbol(c_twf, tw_f, sizeof(float2) * 64);
+  cudaMemcpyToSymbol(c_twd, tw_d, sizeof(double2) * 64);
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Processing-order key (PHASED: phase, I, J; RASTER: I, J).
+__device__ __forceinline__ int64_t order_key(const JobDev& J, int I, int Jb) {
+  int64_t k = ((int64_t)I << 20) | (int64_t)Jb;
+  if (J.order == ORDER_PHASED) k |= (int64_t)((I % J.P) * J.P + (Jb % J.P)) << 40;
+  return k;
+}
+
+// Pops the next ready item: >= 0 item id, -1 queue drained, -2 error.
+__device__ __forceinline__ int queue_pop(const ClassArgs& C, int64_t timeout_ns) {
+  const int n = ld_relaxed(&C.q->n_items);
+  const int pos = atomicAdd(&C.q->head, 1);
+  if (pos >= n) return -1;
+  const uint64_t t0 = global_ns();
+  unsigned sleep_ns = 32;
+  int v;
+  while ((v = ld_acquire(&C.slots[pos])) < 0) {
+    if (ld_relaxed(&C.q->error) != 0) return -2;
+    if ((int64_t)(global_ns() - t0) > timeout_ns) {
+      atomicOr(&C.q->error, ERR_TIMEOUT);
+      C.q->error_info = pos;
+      return -2;
+    }
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 2048) sleep_ns <<= 1;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void queue_push(const ClassArgs& C, int item) {
+  const int pos = atomicAdd(&C.q->tail, 1);
+  st_release(&C.slots[pos], item);
+}
+
+// After a block's writes are globally visible: decrement the pending count
+// of every later lost block in its dependency window, queue those reaching 0.
+__device__ __forceinline__ void release_successors(const ExecArgs& a, const ClassArgs& C, const TileDev& T,
+                                   const JobDev& J, int I, int Jb, int t, int nthr) {
+  if (J.order == ORDER_INDEPENDENT || a.level_mode || a.single_item >= 0) return;
+  const int D = J.D, wd = 2 * D + 1;
+  const int64_t kx = order_key(J, I, Jb);
+  const int32_t* map = a.map + T.map_off;
+  for (int pos = t; pos < wd * wd; pos += nthr) {
+    const int I2 = I + pos / wd - D, J2 = Jb + pos % wd - D;
+    if (I2 < 0 || I2 >= T.nby || J2 < 0 || J2 >= T.nbx) continue;
+    const int id2 = map[I2 * T.nbx + J2];
+    if (id2 < 0 || order_key(J, I2, J2) <= kx) continue;
+    if (atomicSub(&C.cnt[id2], 1) == 1) {
+      __threadfence();
+      queue_push(C, id2);
+    }
+  }
+}
+
+__device__ __forceinline__ uint8_t to_u8(float g) {
+  float c = fminf(fmaxf(g, 0.f), 255.f);
+  return (uint8_t)__float2int_rn(c);  // round half to even
+}
+__device__ __forceinline__ uint8_t to_u8(double g) {
+  double c = fmin(fmax(g, 0.0), 255.0);
+  return (uint8_t)__double2int_rn(c);
+}
+
+// ---------------------------------------------------------------------------
+// Support staging: z(m, n) = (w, w*r) for m, n < S into a swizzled F x F
+// buffer; element (m, n) lives at m*F + (n ^ (m & (F-1))) so that row-wise and
+// column-wise walks of a warp hit distinct banks.
+// ---------------------------------------------------------------------------
+template <int F>
+__device__ __forceinline__ int swz(int m, int n) {
+  return m * F + (n ^ (m & (F - 1)));
+}
+
+template <int F, typename real, typename real2>
+__device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J, const real* val,
+                                              int I, int Jb, real2* zbuf, int t, int nthr) {
+  const int S = J.S;
+  const int oy = I * J.b - J.B, ox = Jb * J.b - J.B;
+  const real* wiso;
+  real delta;
+  if constexpr (sizeof(real) == 4) {
+    wiso = J.wiso_f;
+    delta = J.delta_f;
+  } else {
+    wiso = J.wiso_d;
+    delta = J.delta;
+  }
+  for (int e = t; e < S * S; e += nthr) {
+    const int m = e / S, n = e - m * S;
+    real wv = 0, zr = 0;
+    const int ty = oy + m, tx = ox + n;
+    if (ty >= 0 && ty < T.eh && tx >= 0 && tx < T.ew) {
+      const size_t gi = (size_t)(T.ey + ty) * J.pitch + (T.ex + tx);
+      const real wi = __ldg(wiso + e);
+      if (__ldg(J.mask + gi) == 0) {
+        wv = wi;
+        zr = wi * (real)__ldg(J.image + gi);
+      } else if (J.order != ORDER_INDEPENDENT) {
+        const real v = __ldcg(val + (size_t)ty * T.ew + tx);
+        if (!isnan(v)) {
+          wv = delta * wi;
+          zr = wv * v;
+        }
+      }
+    }
+    real2 z;
+    z.x = wv;
+    z.y = zr;
+    zbuf[swz<F>(m, n)] = z;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Register FFT (radix-2 decimation in time, natural order in and out):
+// X[k] = sum_n x[n] exp(-2 pi i k n / N), N = 32 or 64, fully unrolled.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int brev_c(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+// Bit-reversal permutation as compile-time register renaming.
+template <int I, int N, int LOG>
+struct BitRev {
+  static __device__ __forceinline__ void run(float2 (&x)[N]) {
+    constexpr int J = brev_c(I, LOG);
+    if constexpr (I < J) {
+      const float2 t = x[I];
+      x[I] = x[J];
+      x[J] = t;
+    }
+    BitRev<I + 1, N, LOG>::run(x);
+  }
+};
+template <int N, int LOG>
+struct BitRev<N, N, LOG> {
+  static __device__ __forceinline__ void run(float2 (&)[N]) {}
+};
+
+// One radix-2 stage (butterfly span 2^S); twiddle exp(-2 pi i k / 2^(S+1)).
+template <int S, int N, int LOG>
+struct FftStage {
+  static __device__ __forceinline__ void run(float2 (&x)[N]) {
+    constexpr int half = 1 << S;
+#pragma unroll
+    for (int g = 0; g < N; g += 2 * half) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const float2 a = x[g + k], b = x[g + k + half];
+        float2 tt;
+        if (k == 0) {
+          tt = b;
+        } else {
+          const float2 w = c_twf[k * (32 >> S)];
+          tt = make_float2(w.x * b.x - w.y * b.y, w.x * b.y + w.y * b.x);
+        }
+        x[g + k] = make_float2(a.x + tt.x, a.y + tt.y);
+        x[g + k + half] = make_float2(a.x - tt.x, a.y - tt.y);
+      }
+    }
+    FftStage<S + 1, N, LOG>::run(x);
+  }
+};
+template <int N, int LOG>
+struct FftStage<LOG, N, LOG> {
+  static __device__ __forceinline__ void run(float2 (&)[N]) {}
+};
+
+template <int N>
+__device__ __forceinline__ void fft_reg(float2 (&x)[N]) {
+  constexpr int LOG = (N == 32) ? 5 : 6;
+  BitRev<0, N, LOG>::run(x);
+  FftStage<0, N, LOG>::run(x);
+}
+
+template <bool CTA>
+__device__ __forceinline__ void bar() {
+  if constexpr (CTA) __syncthreads(); else __syncwarp();
+}
+
+// Model evaluation at the block's b x b pixels and write-back (all executors).
+// coef_u / coef_d hold the K selected (u, Delta) pairs; tw[q] = exp(+2 pi i q/64).
+// Threads split the K terms when the block has fewer pixels than threads.
+template <bool CTA, typename real, typename real2>
+__device__ __forceinline__ void eval_and_write(const TileDev& T, const JobDev& J, real* val, int I, int Jb,
+                               const int* coef_u, const real2* coef_d, const real2* tw,
+                               real* red, int t, int nthr) {
+  const int b = J.b, np = b * b, K = J.K, F = J.F, B = J.B;
+  const int tstep = 64 / F;
+  const int nsplit = np <= nthr ? nthr / np : 1;
+  for (int p0 = 0; p0 < np; p0 += nthr / nsplit) {
+    const int p = p0 + t % (nthr / nsplit), s = t / (nthr / nsplit);
+    real g = 0;
+    if (p < np && s < nsplit) {
+      const int m = B + p / b, n = B + p % b;
+      for (int nu = s; nu < K; nu += nsplit) {
+        const int u = coef_u[nu];
+        const int q = (((u / F) * m + (u % F) * n) & (F - 1)) * tstep;
+        const real2 d = coef_d[nu], e = tw[q];
+        g += d.x * e.x - d.y * e.y;
+      }
+    }
+    red[t] = g;
+    bar<CTA>();
+    if (s == 0 && p < np) {
+      for (int k = 1; k < nsplit; ++k) g += red[t + k * (nthr / nsplit)];
+      const int ty = I * b + p / b, tx = Jb * b + p % b;
+      if (ty < T.eh && tx < T.ew) {
+        const int gy = T.ey + ty, gx = T.ex + tx;
+        const size_t gi = (size_t)gy * J.pitch + gx;
+        if (__ldg(J.mask + gi) != 0) {
+          val[(size_t)ty * T.ew + tx] = g;
+          if (gx >= T.x && gx < T.x + T.w && gy >= T.y && gy < T.y + T.h) {
+            J.out[gi] = to_u8(g);
+            if (J.out_f32) J.out_f32[(size_t)gy * J.W + gx] = (float)g;
+            if (J.out_f64) J.out_f64[(size_t)gy * J.W + gx] = (double)g;
+          }
+        }
+      }
+    }
+    bar<CTA>();
+  }
+}
+
+__device__ __forceinline__ void debug_record(const ExecArgs& a, int cls, int id, const TileDev& T,
+                                             int tile, int I, int Jb) {
+  if (a.dbg_rec == nullptr || id >= a.dbg_cap) return;
+  int32_t* r = a.dbg_rec + ((size_t)cls * a.dbg_cap + id) * 4;
+  r[0] = T.job; r[1] = tile; r[2] = I; r[3] = Jb;
+}
+__device__ __forceinline__ void debug_useq(const ExecArgs& a, int cls, int id, int it, int u) {
+  if (a.dbg_useq == nullptr || id >= a.dbg_cap) return;
+  a.dbg_useq[((size_t)cls * a.dbg_cap + id) * KMAX + it] = u;
+}
+
+// Argmax key of one bin: the energy's float bits with the low 10 (F = 32) or
+// 12 (F = 64) mantissa bits replaced by the inverted flat index, so that an
+// integer max picks the largest energy and, among energies equal to the
+// kept precision, the lowest flat index k1*F + k2.
+#define FSE_SEL32(R, j, v)                                              \
+  switch (j) {                                                         \
+    case 0: v = R[0]; break;   case 1: v = R[1]; break;                \
+    case 2: v = R[2]; break;   case 3: v = R[3]; break;                \
+    case 4: v = R[4]; break;   case 5: v = R[5]; break;                \
+    case 6: v = R[6]; break;   case 7: v = R[7]; break;                \
+    case 8: v = R[8]; break;   case 9: v = R[9]; break;                \
+    case 10: v = R[10]; break; case 11: v = R[11]; break;              \
+    case 12: v = R[12]; break; case 13: v = R[13]; break;              \
+    case 14: v = R[14]; break; case 15: v = R[15]; break;              \
+    case 16: v = R[16]; break; case 17: v = R[17]; break;              \
+    case 18: v = R[18]; break; case 19: v = R[19]; break;              \
+    case 20: v = R[20]; break; case 21: v = R[21]; break;              \
+    case 22: v = R[22]; break; case 23: v = R[23]; break;              \
+    case 24: v = R[24]; break; case 25: v = R[25]; break;              \
+    case 26: v = R[26]; break; case 27: v = R[27]; break;              \
+    case 28: v = R[28]; break; case 29: v = R[29]; break;              \
+    case 30: v = R[30]; break; default: v = R[31]; break;              \
+  }
+
+// ===========================================================================
+// Executor 1: FP32, F = 32.  One warp per lost block.  Lane l owns spectrum
+// column k2 = l, bins (k1 = j, l) for j = 0..31 in registers.  W sits in
+// shared memory with its 32 rows stored twice, so W(k - u) for row j is at a
+// per-iteration base plus the compile-time offset j * 32.
+// ===========================================================================
+struct alignas(16) WarpSmem32 {
+  float2 Wd[64 * 32];     // rows 0..63: W rows (r mod 32); 32..63 double as FFT buffer
+  float2 coef_d[KMAX];
+  int32_t coef_u[KMAX];
+  float red[32];
+};
+constexpr int NW32 = 2;  // warps (independent workers) per CTA
+constexpr size_t SMEM32 = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32);
+
+__device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem32& sm, const float2* tw,
+                            int lane) {
+  const ClassArgs& C = a.c[CLS_F32_32];
+  const int2 it = C.items[id];
+  const TileDev T = a.tiles[it.x];
+  const JobDev J = a.jobs[T.job];
+  const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+  const int S = J.S, K = J.K;
+  float* val = a.val_f + T.val_off;
+  if (lane == 0) debug_record(a, CLS_F32_32, id, T, it.x, I, Jb);
+  float2* zbuf = sm.Wd + 32 * 32;
+
+  // stage -> rows 32..63 (swizzled F x F buffer)
+  stage_support<32, float, float2>(T, J, val, I, Jb, zbuf, lane, 32);
+  __syncwarp();
+  float2 x[32];
+  // row FFTs: lane m transforms support row m
+  if (lane < S) {
+#pragma unroll
+    for (int n = 0; n < 32; ++n) x[n] = n < S ? zbuf[swz<32>(lane, n)] : make_float2(0.f, 0.f);
+    fft_reg<32>(x);
+#pragma unroll
+    for (int n = 0; n < 32; ++n) zbuf[swz<32>(lane, n)] = x[n];
+  }
+  __syncwarp();
+  // column FFTs: lane l transforms column l -> x[k1] = Z(k1, l)
+#pragma unroll
+  for (int m = 0; m < 32; ++m) x[m] = m < S ? zbuf[swz<32>(m, lane)] : make_float2(0.f, 0.f);
+  fft_reg<32>(x);
+  __syncwarp();
+  // Hermitian split: W = (Z(k) + conj Z(-k))/2, R = (Z(k) - conj Z(-k))/(2i)
+  const int src = (32 - lane) & 31;
+#pragma unroll
+  for (int j = 0; j <= 16; ++j) {
+    const int j2 = (32 - j) & 31;
+    float2 zm, zm2;
+    zm.x = __shfl_sync(0xffffffffu, x[j2].x, src);
+    zm.y = __shfl_sync(0xffffffffu, x[j2].y, src);
+    zm2.x = __shfl_sync(0xffffffffu, x[j].x, src);
+    zm2.y = __shfl_sync(0xffffffffu, x[j].y, src);
+    const float2 z = x[j], z2 = x[j2];
+    const float2 w = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+    sm.Wd[j * 32 + lane] = w;
+    sm.Wd[(j + 32) * 32 + lane] = w;
+    x[j] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    if (j2 != j) {
+      const float2 w2 = make_float2(0.5f * (z2.x + zm2.x), 0.5f * (z2.y - zm2.y));
+      sm.Wd[j2 * 32 + lane] = w2;
+      sm.Wd[(j2 + 32) * 32 + lane] = w2;
+      x[j2] = make_float2(0.5f * (z2.y + zm2.y), 0.5f * (zm2.x - z2.x));
+    }
+  }
+  __syncwarp();
+  const float W0 = sm.Wd[0].x;
+  if (!(W0 > 0.f)) {  // no usable pixel in the support
+    if (lane == 0) atomicAdd(&C.q->n_empty, 1);
+    return;
+  }
+  const float gs = J.gamma_f / W0;
+  float2(&R)[32] = x;
+
+  uint32_t best = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float e = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
+    best = max(best, (__float_as_uint(e) & 0xFFFFFC00u) | (uint32_t)((31 - j) << 5));
+  }
+  best |= (uint32_t)(31 - lane);
+  for (int iter = 0; iter < K; ++iter) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, off));
+    const int flat = 1023 - (int)(best & 1023u);
+    const int u1 = flat >> 5, u2 = flat & 31;
+    float2 v;
+    FSE_SEL32(R, u1, v);
+    const float rux = __shfl_sync(0xffffffffu, v.x, u2);
+    const float ruy = __shfl_sync(0xffffffffu, v.y, u2);
+    const float dx = gs * rux, dy = gs * ruy;
+    if (lane == 0) {
+      sm.coef_u[iter] = flat;
+      sm.coef_d[iter] = make_float2(dx, dy);
+      debug_useq(a, CLS_F32_32, id, iter, flat);
+    }
+    if (iter + 1 == K) break;
+    const float2* wp = sm.Wd + (32 - u1) * 32 + ((lane - u2) & 31);
+    best = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float2 w = wp[j * 32];
+      float rx = fmaf(-dx, w.x, R[j].x);
+      rx = fmaf(dy, w.y, rx);
+      float ry = fmaf(-dx, w.y, R[j].y);
+      ry = fmaf(-dy, w.x, ry);
+      R[j] = make_float2(rx, ry);
+      const float e = fmaf(ry, ry, rx * rx);
+      best = max(best, (__float_as_uint(e) & 0xFFFFFC00u) | (uint32_t)((31 - j) << 5));
+    }
+    best |= (uint32_t)(31 - lane);
+  }
+  __syncwarp();
+  eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
+                                       32);
+}
+
+__global__ void __launch_bounds__(NW32 * 32, 5) k_exec_f32_32(const __grid_constant__ ExecArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  WarpSmem32* wsm = reinterpret_cast<WarpSmem32*>(smem_raw + 64 * sizeof(float2));
+  for (int q = threadIdx.x; q < 64; q += blockDim.x) tw[q] = make_float2(c_twf[q].x, -c_twf[q].y);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpSmem32& sm = wsm[warp];
+  const ClassArgs& C = a.c[CLS_F32_32];
+  if (a.single_item >= 0) {
+    if (blockIdx.x == 0 && warp == 0) item_f32_32(a, a.single_item, sm, tw, lane);
+    return;
+  }
+  if (a.level_mode) {
+    const int n = C.q->n_items;
+    for (int id = blockIdx.x * NW32 + warp; id < n; id += gridDim.x * NW32)
+      if (a.level_of[(size_t)CLS_F32_32 * a.level_stride + id] == a.level) item_f32_32(a, id, sm, tw, lane);
+    return;
+  }
+  for (;;) {
+    int id = 0;
+    if (lane == 0) id = queue_pop(C, a.timeout_ns);
+    id = __shfl_sync(0xffffffffu, id, 0);
+    if (id < 0) break;
+    item_f32_32(a, id, sm, tw, lane);
+    __threadfence();
+    __syncwarp();
+    const int2 it = C.items[id];
+    const TileDev T = a.tiles[it.x];
+    const JobDev J = a.jobs[T.job];
+    release_successors(a, C, T, J, it.y >> 16, it.y & 0xFFFF, lane, 32);
+    if (lane == 0) atomicAdd(&C.q->n_done, 1);
+  }
+}
+
+// ===========================================================================
+// Executor 2: FP32, F = 64.  Four warps (128 threads) per lost block.  Thread
+// t owns column c = t & 63 and rows k1 = i + 32*(t >> 6), i = 0..31, in
+// registers.  Per iteration: warp argmax, then a 4-way exchange through
+// shared memory behind one barrier (double-buffered by iteration parity).
+// ===========================================================================
+struct alignas(16) CtaSmem64 {
+  float2 Wd[128 * 64];   // rows 0..127: W rows (r mod 64); 64..127 double as FFT buffer
+  float2 coef_d[KMAX];
+  int32_t coef_u[KMAX];
+  float2 tw[64];
+  float red[128];
+  uint32_t xkey[2][4];
+  float2 xval[2][4];
+  int item;
+};
+constexpr size_t SMEM64 = sizeof(CtaSmem64);
+
+__device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64& sm, int t) {
+  const ClassArgs& C = a.c[CLS_F32_64];
+  const int2 it = C.items[id];
+  const TileDev T = a.tiles[it.x];
+  const JobDev J = a.jobs[T.job];
+  const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+  const int S = J.S, K = J.K;
+  float* val = a.val_f + T.val_off;
+  if (t == 0) debug_record(a, CLS_F32_64, id, T, it.x, I, Jb);
+  float2* zbuf = sm.Wd + 64 * 64;
+
+  stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, 128);
+  __syncthreads();
+  {
+    float2 x[64];
+    if (t < S) {  // row FFTs
+#pragma unroll
+      for (int n = 0; n < 64; ++n) x[n] = n < S ? zbuf[swz<64>(t, n)] : make_float2(0.f, 0.f);
+      fft_reg<64>(x);
+#pragma unroll
+      for (int n = 0; n < 64; ++n) zbuf[swz<64>(t, n)] = x[n];
+    }
+    __syncthreads();
+    if (t < 64) {  // column FFTs (in place, own column only)
+#pragma unroll
+      for (int m = 0; m < 64; ++m) x[m] = m < S ? zbuf[swz<64>(m, t)] : make_float2(0.f, 0.f);
+      fft_reg<64>(x);
+#pragma unroll
+      for (int m = 0; m < 64; ++m) zbuf[swz<64>(m, t)] = x[m];
+    }
+    __syncthreads();
+  }
+  const int c = t & 63, hr = t >> 6, lane = t & 31, warp = t >> 5;
+  float2 R[32];
+  {
+    const int cm = (64 - c) & 63;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int k1 = i + 32 * hr, k1m = (64 - k1) & 63;
+      const float2 z = zbuf[swz<64>(k1, c)], zm = zbuf[swz<64>(k1m, cm)];
+      sm.Wd[k1 * 64 + c] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      R[i] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int k1 = i + 32 * hr;
+    sm.Wd[(k1 + 64) * 64 + c] = sm.Wd[k1 * 64 + c];
+  }
+  __syncthreads();
+  const float W0 = sm.Wd[0].x;
+  if (!(W0 > 0.f)) {
+    if (t == 0) atomicAdd(&C.q->n_empty, 1);
+    return;
+  }
+  const float gs = J.gamma_f / W0;
+  const uint32_t tbits = (uint32_t)((1 - hr) << 11) | (uint32_t)(63 - c);
+
+  uint32_t best = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const float e = fmaf(R[i].y, R[i].y, R[i].x * R[i].x);
+    best = max(best, (__float_as_uint(e) & 0xFFFFF000u) | (uint32_t)((31 - i) << 6));
+  }
+  best |= tbits;
+  for (int iter = 0; iter < K; ++iter) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, off));
+    {
+      const int flat = 4095 - (int)(best & 4095u);
+      const int i_w = (flat >> 6) & 31, l_w = flat & 31;
+      float2 v;
+      FSE_SEL32(R, i_w, v);
+      v.x = __shfl_sync(0xffffffffu, v.x, l_w);
+      v.y = __shfl_sync(0xffffffffu, v.y, l_w);
+      if (lane == 0) {
+        sm.xkey[iter & 1][warp] = best;
+        sm.xval[iter & 1][warp] = v;
+      }
+    }
+    __syncthreads();
+    uint32_t kb = sm.xkey[iter & 1][0];
+    int wb = 0;
+#pragma unroll
+    for (int w = 1; w < 4; ++w) {
+      const uint32_t kw = sm.xkey[iter & 1][w];
+      if (kw > kb) { kb = kw; wb = w; }
+    }
+    const float2 ru = sm.xval[iter & 1][wb];
+    const int flat = 4095 - (int)(kb & 4095u);
+    const int u1 = flat >> 6, u2 = flat & 63;
+    const float dx = gs * ru.x, dy = gs * ru.y;
+    if (t == 0) {
+      sm.coef_u[iter] = flat;
+      sm.coef_d[iter] = make_float2(dx, dy);
+      debug_useq(a, CLS_F32_64, id, iter, flat);
+    }
+    if (iter + 1 == K) break;
+    const float2* wp = sm.Wd + (32 * hr - u1 + 64) * 64 + ((c - u2) & 63);
+    best = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float2 w = wp[i * 64];
+      float rx = fmaf(-dx, w.x, R[i].x);
+      rx = fmaf(dy, w.y, rx);
+      float ry = fmaf(-dx, w.y, R[i].y);
+      ry = fmaf(-dy, w.x, ry);
+      R[i] = make_float2(rx, ry);
+      const float e = fmaf(ry, ry, rx * rx);
+      best = max(best, (__float_as_uint(e) & 0xFFFFF000u) | (uint32_t)((31 - i) << 6));
+    }
+    best |= tbits;
+  }
+  __syncthreads();
+  eval_and_write<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
+                                      128);
+}
+
+__global__ void __launch_bounds__(128, 3) k_exec_f32_64(const __grid_constant__ ExecArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CtaSmem64& sm = *reinterpret_cast<CtaSmem64*>(smem_raw);
+  const int t = threadIdx.x;
+  if (t < 64) sm.tw[t] = make_float2(c_twf[t].x, -c_twf[t].y);
+  __syncthreads();
+  const ClassArgs& C = a.c[CLS_F32_64];
+  if (a.single_item >= 0) {
+    if (blockIdx.x == 0) item_f32_64(a, a.single_item, sm, t);
+    return;
+  }
+  if (a.level_mode) {
+    const int n = C.q->n_items;
+    for (int id = blockIdx.x; id < n; id += gridDim.x)
+      if (a.level_of[(size_t)CLS_F32_64 * a.level_stride + id] == a.level) {
+        item_f32_64(a, id, sm, t);
+        __syncthreads();
+      }
+    return;
+  }
+  for (;;) {
+    if (t == 0) sm.item = queue_pop(C, a.timeout_ns);
+    __syncthreads();
+    const int id = sm.item;
+    if (id < 0) break;
+    item_f32_64(a, id, sm, t);
+    __threadfence();
+    __syncthreads();
+    const int2 it = C.items[id];
+    const TileDev T = a.tiles[it.x];
+    const JobDev J = a.jobs[T.job];
+    release_successors(a, C, T, J, it.y >> 16, it.y & 0xFFFF, t, 128);
+    if (t == 0) atomicAdd(&C.q->n_done, 1);
+    __syncthreads();
+  }
+}
+
+// ===========================================================================
+// Executor 3: FP64 validation path (F = 32 or 64).  One CTA of 256 threads
+// per block, spectrum and weight spectrum both in shared memory, FFT lines in
+// shared memory, argmax with the tie rule "lowest flat index among
+// |R|^2 >= (1 - tau) max |R|^2" (tau = 1e-9).  Same staging, model and
+// write-back code as the FP32 executors.
+// ===========================================================================
+constexpr int NT64 = 256;
+struct alignas(16) CtaSmemD {
+  double2 R[64 * 64];
+  double2 Wb[64 * 64];
+  double2 coef_d[KMAX];
+  int32_t coef_u[KMAX];
+  double2 tw[64];
+  double red[NT64];
+  int32_t redi[NT64];
+  int item;
+};
+constexpr size_t SMEMD = sizeof(CtaSmemD);
+
+// In-place radix-2 DIT FFT of one line of n = 32/64 elements at stride `st`.
+__device__ void fft_line_d(double2* x, int st, int n, int logn) {
+  for (int i = 0; i < n; ++i) {
+    int j = 0;
+    for (int b = 0; b < logn; ++b) j |= ((i >> b) & 1) << (logn - 1 - b);
+    if (i < j) {
+      const double2 tmp = x[i * st];
+      x[i * st] = x[j * st];
+      x[j * st] = tmp;
+    }
+  }
+  for (int s = 0; s < logn; ++s) {
+    const int half = 1 << s;
+    for (int g = 0; g < n; g += 2 * half)
+      for (int k = 0; k < half; ++k) {
+        const double2 w = c_twd[k * (32 >> s)];
+        const double2 a = x[(g + k) * st], b = x[(g + k + half) * st];
+        const double2 tt = make_double2(w.x * b.x - w.y * b.y, w.x * b.y + w.y * b.x);
+        x[(g + k) * st] = make_double2(a.x + tt.x, a.y + tt.y);
+        x[(g + k + half) * st] = make_double2(a.x - tt.x, a.y - tt.y);
+      }
+  }
+}
+
+__device__ __forceinline__ void item_f64(const ExecArgs& a, int id, CtaSmemD& sm, int t) {
+  const ClassArgs& C = a.c[CLS_F64];
+  const int2 it = C.items[id];
+  const TileDev T = a.tiles[it.x];
+  const JobDev J = a.jobs[T.job];
+  const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+  const int S = J.S, K = J.K, F = J.F, FF = F * F, logF = F == 32 ? 5 : 6;
+  double* val = a.val_d + T.val_off;
+  if (t == 0) debug_record(a, CLS_F64, id, T, it.x, I, Jb);
+  // stage into a plain (unswizzled) F x F buffer
+  for (int e = t; e < FF; e += NT64) sm.R[e] = make_double2(0.0, 0.0);
+  __syncthreads();
+  {
+    const int oy = I * J.b - J.B, ox = Jb * J.b - J.B;
+    for (int e = t; e < S * S; e += NT64) {
+      const int m = e / S, n = e - m * S;
+      double wv = 0, zr = 0;
+      const int ty = oy + m, tx = ox + n;
+      if (ty >= 0 && ty < T.eh && tx >= 0 && tx < T.ew) {
+        const size_t gi = (size_t)(T.ey + ty) * J.pitch + (T.ex + tx);
+        const double wi = J.wiso_d[e];
+        if (__ldg(J.mask + gi) == 0) {
+          wv = wi;
+          zr = wi * (double)__ldg(J.image + gi);
+        } else if (J.order != ORDER_INDEPENDENT) {
+          const double v = __ldcg(val + (size_t)ty * T.ew + tx);
+          if (!isnan(v)) {
+            wv = J.delta * wi;
+            zr = wv * v;
+          }
+        }
+      }
+      sm.R[m * F + n] = make_double2(wv, zr);
+    }
+  }
+  __syncthreads();
+  if (t < F) fft_line_d(sm.R + t * F, 1, F, logF);
+  __syncthreads();
+  if (t < F) fft_line_d(sm.R + t, F, F, logF);
+  __syncthreads();
+  // Hermitian split, pairwise in place
+  for (int k = t; k < FF; k += NT64) {
+    const int k1 = k / F, k2 = k % F;
+    const int km = ((F - k1) & (F - 1)) * F + ((F - k2) & (F - 1));
+    if (km < k) continue;
+    const double2 z = sm.R[k], zm = sm.R[km];
+    sm.Wb[k] = make_double2(0.5 * (z.x + zm.x), 0.5 * (z.y - zm.y));
+    sm.Wb[km] = make_double2(0.5 * (zm.x + z.x), 0.5 * (zm.y - z.y));
+    sm.R[k] = make_double2(0.5 * (z.y + zm.y), 0.5 * (zm.x - z.x));
+    sm.R[km] = make_double2(0.5 * (zm.y + z.y), 0.5 * (z.x - zm.x));
+  }
+  __syncthreads();
+  const double W0 = sm.Wb[0].x;
+  if (!(W0 > 0.0)) {
+    if (t == 0) atomicAdd(&C.q->n_empty, 1);
+    return;
+  }
+  const double gs = J.gamma / W0;
+  for (int iter = 0; iter < K; ++iter) {
+    double emax = 0;
+    for (int k = t; k < FF; k += NT64) emax = fmax(emax, sm.R[k].x * sm.R[k].x + sm.R[k].y * sm.R[k].y);
+    sm.red[t] = emax;
+    __syncthreads();
+    for (int s = NT64 / 2; s > 0; s >>= 1) {
+      if (t < s) sm.red[t] = fmax(sm.red[t], sm.red[t + s]);
+      __syncthreads();
+    }
+    const double thr = (1.0 - TAU_F64) * sm.red[0];
+    int kmin = FF;
+    for (int k = t; k < FF; k += NT64)
+      if (sm.R[k].x * sm.R[k].x + sm.R[k].y * sm.R[k].y >= thr) { kmin = k; break; }
+    sm.redi[t] = kmin;
+    __syncthreads();
+    for (int s = NT64 / 2; s > 0; s >>= 1) {
+      if (t < s) sm.redi[t] = min(sm.redi[t], sm.redi[t + s]);
+      __syncthreads();
+    }
+    const int u = sm.redi[0];
+    const double2 ru = sm.R[u];
+    const double dx = gs * ru.x, dy = gs * ru.y;
+    __syncthreads();
+    if (t == 0) {
+      sm.coef_u[iter] = u;
+      sm.coef_d[iter] = make_double2(dx, dy);
+      debug_useq(a, CLS_F64, id, iter, u);
+    }
+    const int u1 = u / F, u2 = u % F;
+    for (int k = t; k < FF; k += NT64) {
+      const int k1 = k / F, k2 = k % F;
+      const double2 w = sm.Wb[((k1 - u1) & (F - 1)) * F + ((k2 - u2) & (F - 1))];
+      double2 r = sm.R[k];
+      r.x -= dx * w.x - dy * w.y;
+      r.y -= dx * w.y + dy * w.x;
+      sm.R[k] = r;
+    }
+    __syncthreads();
+  }
+  eval_and_write<true, double, double2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
+                                        NT64);
+}
+
+__global__ void __launch_bounds__(NT64) k_exec_f64(const __grid_constant__ ExecArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CtaSmemD& sm = *reinterpret_cast<CtaSmemD*>(smem_raw);
+  const int t = threadIdx.x;
+  if (t < 64) sm.tw[t] = make_double2(c_twd[t].x, -c_twd[t].y);
+  __syncthreads();
+  const ClassArgs& C = a.c[CLS_F64];
+  if (a.single_item >= 0) {
+    if (blockIdx.x == 0) item_f64(a, a.single_item, sm, t);
+    return;
+  }
+  if (a.level_mode) {
+    const int n = C.q->n_items;
+    for (int id = blockIdx.x; id < n; id += gridDim.x)
+      if (a.level_of[(size_t)CLS_F64 * a.level_stride + id] == a.level) {
+        item_f64(a, id, sm, t);
+        __syncthreads();
+      }
+    return;
+  }
+  for (;;) {
+    if (t == 0) sm.item = queue_pop(C, a.timeout_ns);
+    __syncthreads();
+    const int id = sm.item;
+    if (id < 0) break;
+    item_f64(a, id, sm, t);
+    __threadfence();
+    __syncthreads();
+    const int2 it = C.items[id];
+    const TileDev T = a.tiles[it.x];
+    const JobDev J = a.jobs[T.job];
+    release_successors(a, C, T, J, it.y >> 16, it.y & 0xFFFF, t, NT64);
+    if (t == 0) atomicAdd(&C.q->n_done, 1);
+    __syncthreads();
+  }
+}
+
+// ===========================================================================
+// Planner kernels
+// ===========================================================================
+
+// out = mask ? 0 : image; out_f32 likewise.  grid.y = job.
+__global__ void k_init_out(const JobDev* jobs) {
+  const JobDev J = jobs[blockIdx.y];
+  const int64_t npx = (int64_t)J.W * J.H;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npx;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(p / J.W), x = (int)(p - (int64_t)y * J.W);
+    const size_t gi = (size_t)y * J.pitch + x;
+    const uint8_t v = J.mask[gi] ? 0 : J.image[gi];
+    J.out[gi] = v;
+    if (J.out_f32) J.out_f32[p] = (float)v;
+    if (J.out_f64) J.out_f64[p] = (double)v;
+  }
+}
+
+// One thread per block of a tile's grid: lost if any pixel of the block
+// (inside the extended tile) is lost.  grid.y = tile.
+__global__ void k_mark(const __grid_constant__ ExecArgs a) {
+  const TileDev T = a.tiles[blockIdx.y];
+  const JobDev J = a.jobs[T.job];
+  const int nb = T.nbx * T.nby;
+  const ClassArgs& C = a.c[T.cls];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    const int I = k / T.nbx, Jb = k - I * T.nbx;
+    bool lost = false, core = false;
+    const int y0 = I * J.b, x0 = Jb * J.b;
+    for (int yy = y0; yy < min(y0 + J.b, T.eh); ++yy)
+      for (int xx = x0; xx < min(x0 + J.b, T.ew); ++xx) {
+        const int gy = T.ey + yy, gx = T.ex + xx;
+        if (J.mask[(size_t)gy * J.pitch + gx]) {
+          lost = true;
+          if (gx >= T.x && gx < T.x + T.w && gy >= T.y && gy < T.y + T.h) core = true;
+        }
+      }
+    int id = -1;
+    if (lost) {
+      id = atomicAdd(&C.q->n_items, 1);
+      if (id < C.cap) {
+        C.items[id] = make_int2(blockIdx.y, (I << 16) | Jb);
+        if (core) atomicAdd(&C.q->n_core, 1);
+      } else {
+        atomicOr(&C.q->error, ERR_BOUNDS);
+        id = -1;
+      }
+    }
+    a.map[T.map_off + k] = id;
+  }
+}
+
+// Pending-predecessor count of every item; items without any are queued.
+__global__ void k_deps(const __grid_constant__ ExecArgs a, int cls) {
+  const ClassArgs& C = a.c[cls];
+  const int n = min(C.q->n_items, C.cap);
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+    const int2 it = C.items[id];
+    const TileDev T = a.tiles[it.x];
+    const JobDev J = a.jobs[T.job];
+    const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+    int cnt = 0;
+    if (J.order != ORDER_INDEPENDENT) {
+      const int D = J.D;
+      const int64_t kx = order_key(J, I, Jb);
+      const int32_t* map = a.map + T.map_off;
+      for (int dI = -D; dI <= D; ++dI)
+        for (int dJ = -D; dJ <= D; ++dJ) {
+          const int I2 = I + dI, J2 = Jb + dJ;
+          if (I2 < 0 || I2 >= T.nby || J2 < 0 || J2 >= T.nbx) continue;
+          const int id2 = map[I2 * T.nbx + J2];
+          if (id2 >= 0 && order_key(J, I2, J2) < kx) ++cnt;
+        }
+    }
+    C.cnt[id] = cnt;
+    if (a.level_of) a.level_of[(size_t)cls * a.level_stride + id] =
+        J.order == ORDER_PHASED ? (I % J.P) * J.P + (Jb % J.P) : 0;
+    if (cnt == 0) queue_push(C, id);
+  }
+}
+
+__global__ void k_probe(const __grid_constant__ ExecArgs a) {
+  const int id = queue_pop(a.c[0], a.timeout_ns);
+  if (id >= 0) atomicAdd(&a.c[0].q->n_done, 1);
+}
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+int exec_threads(int cls) { return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? 128 : NT64); }
+size_t exec_smem(int cls) { return cls == CLS_F32_32 ? SMEM32 : (cls == CLS_F32_64 ? SMEM64 : SMEMD); }
+const void* exec_kernel_ptr(int cls) {
+  return cls == CLS_F32_32 ? (const void*)k_exec_f32_32
+                           : (cls == CLS_F32_64 ? (const void*)k_exec_f32_64 : (const void*)k_exec_f64);
+}
+
+cudaError_t exec_setup(int device) {
+  (void)device;
+  cudaError_t e = cudaFuncSetAttribute(k_exec_f32_32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM32);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_exec_f32_64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM64);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_exec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEMD);
+}
+
+cudaError_t launch_init_out(const JobDev* jobs_dev, int n_jobs, int max_pixels, cudaStream_t st) {
+  if (n_jobs == 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min(1024, (max_pixels + 255) / 256 + 1), (unsigned)n_jobs);
+  k_init_out<<<grid, 256, 0, st>>>(jobs_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark(const ExecArgs& a, int n_tiles, int max_tile_blocks, cudaStream_t st) {
+  if (n_tiles == 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min(4096, (max_tile_blocks + 255) / 256 + 1), (unsigned)n_tiles);
+  k_mark<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st) {
+  if (cap == 0) return cudaSuccess;
+  k_deps<<<(unsigned)std::min(8192, (cap + 255) / 256), 256, 0, st>>>(a, cls);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  if (cls == CLS_F32_32) k_exec_f32_32<<<grid, NW32 * 32, SMEM32, st>>>(a);
+  else if (cls == CLS_F32_64) k_exec_f32_64<<<grid, 128, SMEM64, st>>>(a);
+  else k_exec_f64<<<grid, NT64, SMEMD, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st) {
+  k_probe<<<1, 1, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace fse

@@ -1,0 +1,205 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GPU).
+
+FP32 path: per-config max |err| <= 1.0 grey level and |delta PSNR| <= 0.05 dB
+against the oracle's reconstruction.  FP64 device path: the same selected
+bin sequence per block as the oracle and model values within 1e-9.
+"""
+import numpy as np
+import pytest
+
+import paper_2207_00238_gb300 as fse
+from paper_2207_00238_gb300 import synth
+from tests.gpu_util import oracle_run, psnr, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL_ERR = 1.0
+TOL_DPSNR = 0.05
+TOL_F64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    fse.build()
+    c = fse.Context(0, arena_bytes=1 << 30)
+    yield c
+    c.close()
+
+
+def _small_tiled(W=128, H=96, K=60, n_tiles=4, seed=synth.SEED_BASE + 20):
+    return synth.tiled_1024(seed=seed, W=W, H=H, K=K, n_tiles=n_tiles)[0]
+
+
+def _defects(W=96, H=72, seed=synth.SEED_BASE + 30, cols=2):
+    rng = synth.Rng(seed)
+    img = synth.image(W, H, rng, structure=True)
+    mask = synth.defect_mask(W, H, 0.01, cols, rng)
+    return dict(image=img, mask=mask, params=synth.params(4, 14, 32, 100, n_tiles=2, overlap=16))
+
+
+CASES = {
+    "plain_64": lambda: synth.plain_64()[0],
+    "tiled_small_f64": lambda: _small_tiled(),
+    "defects_small": lambda: _defects(),
+}
+
+
+def _fp32_check(oracle_lib, job, got):
+    ref = oracle_run(oracle_lib, job, report=False)
+    lost = job["mask"] > 0
+    err = np.abs(got["out"].astype(int) - ref["out"].astype(int))[lost]
+    p_gpu = psnr(got["out"], job["image"], lost)
+    p_ref = psnr(ref["out"], job["image"], lost)
+    assert (got["out"][~lost] == job["image"][~lost]).all()
+    assert err.max() <= TOL_ERR, f"max |err| {err.max()}"
+    assert abs(p_gpu - p_ref) <= TOL_DPSNR, f"PSNR gpu {p_gpu:.4f} oracle {p_ref:.4f}"
+    return err.max(), p_gpu - p_ref
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp32_within_tolerance(ctx, oracle_lib, case):
+    job = CASES[case]()
+    got, st = run_gpu(ctx, [job])
+    assert st["lost_blocks"] > 0
+    _fp32_check(oracle_lib, job, got[0])
+
+
+def _seq_check(oracle_lib, ctx, job, **over):
+    job = dict(job)
+    job["params"] = dict(job["params"], **over)
+    ctx.set_option(fse.OPT_DEBUG_CAPTURE, 1)
+    try:
+        got, st = run_gpu(ctx, [job], precision=64, f64=True)
+        rec, useq = ctx.debug_fetch(int(st["lost_blocks"]) + 8)
+    finally:
+        ctx.set_option(fse.OPT_DEBUG_CAPTURE, 0)
+    ref = oracle_run(oracle_lib, job, report=True)
+    assert len(rec) == len(ref["blocks"]) == st["lost_blocks"]
+    want = {(int(t), int(i), int(j)): tuple(s) for (t, i, j, _), s in zip(ref["blocks"], ref["useq"])}
+    have = {(int(r[1]), int(r[2]), int(r[3])): tuple(s) for r, s in zip(rec, useq)}
+    assert have.keys() == want.keys()
+    bad = [k for k in want if have[k] != want[k]]
+    assert not bad, f"{len(bad)} of {len(want)} blocks differ, e.g. {bad[0]}"
+    lost = job["mask"] > 0
+    np.testing.assert_allclose(got[0]["g"][lost], ref["g"][lost], rtol=0, atol=TOL_F64)
+    assert (got[0]["out"] == ref["out"]).all()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_selection_sequence(ctx, oracle_lib, case):
+    _seq_check(oracle_lib, ctx, CASES[case]())
+
+
+@pytest.mark.parametrize("order", ["raster", "independent"])
+def test_fp64_orders(ctx, oracle_lib, order):
+    _seq_check(oracle_lib, ctx, _defects(W=80, H=56, cols=1), order=order)
+    _seq_check(oracle_lib, ctx, _small_tiled(W=96, H=80, K=30, n_tiles=2), order=order)
+
+
+@pytest.mark.parametrize("order", ["raster", "independent"])
+def test_fp32_orders(ctx, oracle_lib, order):
+    job = _defects(W=80, H=56, cols=1)
+    job["params"] = dict(job["params"], order=order)
+    got, _ = run_gpu(ctx, [job])
+    _fp32_check(oracle_lib, job, got[0])
+
+
+def test_exec_modes_bitwise_equal(ctx):
+    jobs = [_defects(), _small_tiled()]
+    outs = {}
+    for mode in ["dag", "levels", "per_block"]:
+        ctx.exec_mode(mode)
+        try:
+            got, st = run_gpu(ctx, jobs)
+        finally:
+            ctx.exec_mode("dag")
+        outs[mode] = got
+    for mode in ["levels", "per_block"]:
+        for a, b in zip(outs["dag"], outs[mode]):
+            assert (a["out"] == b["out"]).all() and (a["g"] == b["g"]).all()
+
+
+def test_batch_equals_alone(ctx):
+    jobs = [_defects(), _small_tiled(), synth.plain_64()[0], _small_tiled(W=70, H=50, n_tiles=1)]
+    mixed, st = run_gpu(ctx, jobs)
+    assert st["jobs"] == 4
+    for j, m in zip(jobs, mixed):
+        alone, _ = run_gpu(ctx, [j])
+        assert (alone[0]["out"] == m["out"]).all() and (alone[0]["g"] == m["g"]).all()
+
+
+def test_host_path_equals_device_path(ctx):
+    job = _small_tiled()
+    dev, _ = run_gpu(ctx, [job])
+    out = np.zeros_like(job["image"])
+    g = np.zeros(job["image"].shape, np.float32)
+    ctx.extrapolate_host([fse.make_job(job["image"], job["mask"], out, job["params"], out_f32=g)])
+    assert (out == dev[0]["out"]).all() and (g == dev[0]["g"]).all()
+
+
+def test_graph_replay(ctx):
+    import torch
+    job = _defects()
+    ref, _ = run_gpu(ctx, [job])
+    dev = torch.device("cuda", 0)
+    img = torch.from_numpy(job["image"]).to(dev)
+    msk = torch.from_numpy(job["mask"]).to(dev)
+    out = torch.zeros_like(img)
+    cj = [fse.make_job(img, msk, out, job["params"])]
+    ctx.set_option(fse.OPT_USE_GRAPH, 1)
+    try:
+        for _ in range(3):
+            out.zero_()
+            ctx.extrapolate(cj, stats=False)
+            torch.cuda.synchronize()
+            assert (out.cpu().numpy() == ref[0]["out"]).all()
+    finally:
+        ctx.set_option(fse.OPT_USE_GRAPH, 0)
+
+
+def test_edge_cases(ctx, oracle_lib):
+    rng = synth.Rng(synth.SEED_BASE + 40)
+    img = synth.image(45, 37, rng)  # ragged: not a multiple of the block size
+    # nothing lost: output == input, no blocks
+    job = dict(image=img, mask=np.zeros_like(img), params=synth.params(4, 14, 32, 50, n_tiles=3, overlap=8))
+    got, st = run_gpu(ctx, [job])
+    assert st["lost_blocks"] == 0 and (got[0]["out"] == img).all()
+    # everything lost: every support is empty, output 0
+    job = dict(image=img, mask=np.ones_like(img), params=synth.params(4, 14, 32, 50))
+    got, st = run_gpu(ctx, [job])
+    assert st["empty_blocks"] == st["lost_blocks"] > 0 and (got[0]["out"] == 0).all()
+    # image smaller than one support, portrait, ragged, several tiles
+    img = synth.image(21, 53, rng)
+    mask = np.zeros_like(img)
+    mask[10:14, 3:9] = 1
+    mask[40, 17] = 1
+    job = dict(image=img, mask=mask, params=synth.params(8, 16, 64, 40, n_tiles=3, overlap=5))
+    got, _ = run_gpu(ctx, [job])
+    _fp32_check(oracle_lib, job, got[0])
+    _seq_check(oracle_lib, ctx, job)
+
+
+def test_invalid_jobs_rejected(ctx):
+    import torch
+    img = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
+    for bad in [dict(fft=16), dict(fft=32, border=16), dict(K=300), dict(rho=0.0), dict(gamma=2.0),
+                dict(block=0), dict(precision=16)]:
+        p = dict(synth.params(4, 14, 32, 10))
+        p.update(bad)
+        with pytest.raises(fse.FseError) as e:
+            ctx.extrapolate([fse.make_job(img, img, img, p)])
+        assert e.value.code == fse.EINVAL
+    p = synth.params(4, 2, 32, 10, n_tiles=23)
+    img = torch.zeros((32, 32), dtype=torch.uint8, device="cuda")
+    with pytest.raises(fse.FseError) as e:
+        ctx.extrapolate([fse.make_job(img, img, img, p)])
+    assert e.value.code == fse.EDEGENERATE
+
+
+def test_bounded_wait_times_out_and_context_survives(ctx):
+    assert ctx.wait_probe(20000) == fse.ETIMEOUT
+    job = synth.plain_64()[0]
+    got, st = run_gpu(ctx, [job])
+    assert st["lost_blocks"] == 26
