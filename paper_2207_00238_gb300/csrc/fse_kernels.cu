@@ -68,7 +68,7 @@ __device__ __forceinline__ int64_t order_key(const JobDev& J, int I, int Jb) {
 
 // Pops the next ready item: >= 0 item id, -1 queue drained, -2 error.
 __device__ __forceinline__ int queue_pop(const ClassArgs& C, int64_t timeout_ns) {
-  const int n = ld_relaxed(&C.q->n_items);
+  const int n = min(ld_relaxed(&C.q->n_items), C.cap);
   const int pos = atomicAdd(&C.q->head, 1);
   if (pos >= n) return -1;
   const uint64_t t0 = global_ns();
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(NW32 * 32, 5) k_exec_f32_32(const __grid_const
     return;
   }
   if (a.level_mode) {
-    const int n = C.q->n_items;
+    const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x * NW32 + warp; id < n; id += gridDim.x * NW32)
       if (a.level_of[(size_t)CLS_F32_32 * a.level_stride + id] == a.level) item_f32_32(a, id, sm, tw, lane);
     return;
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(128, 3) k_exec_f32_64(const __grid_constant__ 
     return;
   }
   if (a.level_mode) {
-    const int n = C.q->n_items;
+    const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x; id < n; id += gridDim.x)
       if (a.level_of[(size_t)CLS_F32_64 * a.level_stride + id] == a.level) {
         item_f32_64(a, id, sm, t);
@@ -803,7 +803,7 @@ __global__ void __launch_bounds__(NT64) k_exec_f64(const __grid_constant__ ExecA
     return;
   }
   if (a.level_mode) {
-    const int n = C.q->n_items;
+    const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x; id < n; id += gridDim.x)
       if (a.level_of[(size_t)CLS_F64 * a.level_stride + id] == a.level) {
         item_f64(a, id, sm, t);
