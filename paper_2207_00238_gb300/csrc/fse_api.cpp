@@ -159,6 +159,7 @@ int context_create(Context** out, int device, size_t arena_bytes, const char* tu
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev2);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev3);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     context_destroy(c);
     return cuda_fail(e, "context setup");
@@ -187,6 +188,7 @@ void context_destroy(Context* c) {
   if (c->ev2) cudaEventDestroy(c->ev2);
   if (c->ev3) cudaEventDestroy(c->ev3);
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 
@@ -434,7 +436,7 @@ static int run_per_block(Context* c, const Plan& P, const ExecArgs& a, cudaStrea
   QueueDev q[MAX_CLS];
   FSE_CUDA(cudaMemcpyAsync(q, a.c[0].q, sizeof(q), cudaMemcpyDeviceToHost, st));
   FSE_CUDA(cudaStreamSynchronize(st));
-  struct Ent { int64_t key; int cls, id; };
+  struct Ent { int job, tile, phase, I, J, cls, id; };
   std::vector<Ent> ents;
   for (int k = 0; k < MAX_CLS; ++k) {
     const int n = std::min<int64_t>(q[k].n_items, P.cap[k]);
@@ -445,13 +447,17 @@ static int run_per_block(Context* c, const Plan& P, const ExecArgs& a, cudaStrea
       const TileDev& T = P.tiles[items[id].x];
       const JobDev& J = P.jobs[T.job];
       const int I = items[id].y >> 16, Jb = items[id].y & 0xFFFF;
-      int64_t key = ((int64_t)T.job << 52) | ((int64_t)items[id].x << 40);
-      int64_t ok = ((int64_t)I << 20) | Jb;
-      if (J.order == ORDER_PHASED) ok |= (int64_t)((I % J.P) * J.P + (Jb % J.P)) << 36;
-      ents.push_back({key | ok, k, id});
+      const int ph = J.order == ORDER_PHASED ? (I % J.P) * J.P + (Jb % J.P) : 0;
+      ents.push_back({T.job, items[id].x, ph, I, Jb, k, id});
     }
   }
-  std::sort(ents.begin(), ents.end(), [](const Ent& x, const Ent& y) { return x.key < y.key; });
+  std::sort(ents.begin(), ents.end(), [](const Ent& x, const Ent& y) {
+    if (x.job != y.job) return x.job < y.job;
+    if (x.tile != y.tile) return x.tile < y.tile;
+    if (x.phase != y.phase) return x.phase < y.phase;
+    if (x.I != y.I) return x.I < y.I;
+    return x.J < y.J;
+  });
   for (const Ent& e : ents) {
     ExecArgs b = a;
     b.single_item = e.id;
@@ -508,11 +514,11 @@ int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse
       if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
       c->graph_exec = nullptr;
       cudaGraph_t g;
-      FSE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      FSE_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       c->capturing = 1;
-      rc = enqueue(c, P, a, st, &launches, false);
+      rc = enqueue(c, P, a, c->cap_stream, &launches, false);
       c->capturing = 0;
-      cudaError_t e = cudaStreamEndCapture(st, &g);
+      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
       if (rc) return rc;
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
       e = cudaGraphInstantiate(&c->graph_exec, g, 0);

@@ -18,6 +18,7 @@ struct fse_context {
   char* host_buf = nullptr;  // pinned staging of the per-call tables
   size_t host_cap = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  cudaStream_t cap_stream = nullptr;  // graph capture happens here, replay on the caller's stream
   // options
   int exec_mode = FSE_EXEC_DAG;
   int timeout_ms = 20000;
