@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 SMEM_BYTES_PER_CLK_SM = 128  # shared-memory bandwidth per SM per clock
 BYTES_PER_BIN_ITER = 8       # the gathered complex FP32 W(k-u) value
 
@@ -37,14 +37,15 @@ BYTES_PER_BIN_ITER = 8       # the gathered complex FP32 W(k-u) value
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tiled_1024")
     ap.add_argument("--mode", default="dag", choices=["dag", "levels", "per_block"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--arena-mb", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -192,7 +193,7 @@ def main():
     fse.build()
     jobs = workload(args.workload)
     dev = torch.device("cuda", local)
-    ctx = fse.Context(local, arena_bytes=4 << 30)
+    ctx = fse.Context(local, arena_bytes=args.arena_mb << 20)
     ctx.exec_mode(args.mode)
     keep, cjobs, pix = [], [], 0
     for j in jobs:
@@ -274,7 +275,7 @@ def main():
             hout = torch.empty_like(himg).pin_memory()
             hkeep += [himg, hmsk, hout]
             hj.append(fse.make_job(himg.numpy(), hmsk.numpy(), hout.numpy(), j["params"]))
-        e2e_ctx = fse.Context(local, arena_bytes=4 << 30)
+        e2e_ctx = fse.Context(local, arena_bytes=args.arena_mb << 20)
         for _ in range(args.warmup):
             e2e_ctx.extrapolate_host(hj, stream=sptr)
         if dist:
@@ -303,7 +304,7 @@ def main():
     if rank == 0:
         cfg = describe(args.workload, jobs)
         cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                    "exec_mode": args.mode, "l2": "flushed between steps (512 MB write)",
+                    "exec_mode": args.mode, "l2": "flushed between steps (256 MB write)",
                     "lost_blocks_per_step": blocks, "core_lost_blocks_per_step": core_blocks,
                     "bin_iterations_per_step": bins})
         line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,
