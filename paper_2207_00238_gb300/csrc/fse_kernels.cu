@@ -234,6 +234,32 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[N]) {
   FftStage<0, N, LOG>::run(x);
 }
 
+// Copies a descriptor into shared memory word by word (t of nthr threads).
+template <typename T_>
+__device__ __forceinline__ void copy_desc(T_* dst, const T_* src, int t, int nthr) {
+  static_assert(sizeof(T_) % 4 == 0, "descriptor size");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = t; i < (int)(sizeof(T_) / 4); i += nthr) d[i] = __ldg(s + i);
+}
+
+// Second radix-2 step of a 64-point transform split over lanes l and l ^ 16:
+// lane half h = 0 holds E = FFT32(even samples), h = 1 holds O = FFT32(odd
+// samples); afterwards half h holds X[k + 32h], k = 0..31.
+__device__ __forceinline__ void fft64_combine(float2 (&x)[32], int h) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const float2 w = c_twf[k];
+    const float2 o = x[k];
+    const float2 t = make_float2(w.x * o.x - w.y * o.y, w.x * o.y + w.y * o.x);
+    const float2 own = h ? t : o;
+    float2 rcv;
+    rcv.x = __shfl_xor_sync(0xffffffffu, own.x, 16);
+    rcv.y = __shfl_xor_sync(0xffffffffu, own.y, 16);
+    x[k] = h ? make_float2(rcv.x - own.x, rcv.y - own.y) : make_float2(own.x + rcv.x, own.y + rcv.y);
+  }
+}
+
 template <bool CTA>
 __device__ __forceinline__ void bar() {
   if constexpr (CTA) __syncthreads(); else __syncwarp();
@@ -329,6 +355,8 @@ struct alignas(16) WarpSmem32 {
   float2 coef_d[KMAX];
   int32_t coef_u[KMAX];
   float red[32];
+  TileDev T;              // descriptors of the current block's tile and job
+  JobDev J;
 };
 constexpr int NW32 = 2;  // warps (independent workers) per CTA
 constexpr size_t SMEM32 = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32);
@@ -337,8 +365,12 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
                             int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
   const int2 it = C.items[id];
-  const TileDev T = a.tiles[it.x];
-  const JobDev J = a.jobs[T.job];
+  copy_desc(&sm.T, a.tiles + it.x, lane, 32);
+  __syncwarp();
+  copy_desc(&sm.J, a.jobs + sm.T.job, lane, 32);
+  __syncwarp();
+  const TileDev& T = sm.T;
+  const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
   const int S = J.S, K = J.K;
   float* val = a.val_f + T.val_off;
@@ -394,16 +426,15 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
   const float gs = J.gamma_f / W0;
   float2(&R)[32] = x;
 
-  uint32_t best = 0;
+  uint32_t bq[4] = {0u, 0u, 0u, 0u};  // four independent max chains
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const float e = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
-    best = max(best, (__float_as_uint(e) & 0xFFFFFC00u) | (uint32_t)((31 - j) << 5));
+    bq[j & 3] = max(bq[j & 3], (__float_as_uint(e) & 0xFFFFFC00u) | (uint32_t)((31 - j) << 5));
   }
-  best |= (uint32_t)(31 - lane);
+  uint32_t best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | (uint32_t)(31 - lane);
   for (int iter = 0; iter < K; ++iter) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, off));
+    best = __reduce_max_sync(0xffffffffu, best);
     const int flat = 1023 - (int)(best & 1023u);
     const int u1 = flat >> 5, u2 = flat & 31;
     float2 v;
@@ -418,7 +449,7 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
     }
     if (iter + 1 == K) break;
     const float2* wp = sm.Wd + (32 - u1) * 32 + ((lane - u2) & 31);
-    best = 0;
+    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const float2 w = wp[j * 32];
@@ -428,9 +459,9 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
       ry = fmaf(-dy, w.x, ry);
       R[j] = make_float2(rx, ry);
       const float e = fmaf(ry, ry, rx * rx);
-      best = max(best, (__float_as_uint(e) & 0xFFFFFC00u) | (uint32_t)((31 - j) << 5));
+      bq[j & 3] = max(bq[j & 3], (__float_as_uint(e) & 0xFFFFFC00u) | (uint32_t)((31 - j) << 5));
     }
-    best |= (uint32_t)(31 - lane);
+    best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | (uint32_t)(31 - lane);
   }
   __syncwarp();
   eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
@@ -465,9 +496,8 @@ __global__ void __launch_bounds__(NW32 * 32, 5) k_exec_f32_32(const __grid_const
     __threadfence();
     __syncwarp();
     const int2 it = C.items[id];
-    const TileDev T = a.tiles[it.x];
-    const JobDev J = a.jobs[T.job];
-    release_successors(a, C, T, J, it.y >> 16, it.y & 0xFFFF, lane, 32);
+    release_successors(a, C, sm.T, sm.J, it.y >> 16, it.y & 0xFFFF, lane, 32);
+    __syncwarp();
     if (lane == 0) atomicAdd(&C.q->n_done, 1);
   }
 }
@@ -484,17 +514,23 @@ struct alignas(16) CtaSmem64 {
   int32_t coef_u[KMAX];
   float2 tw[64];
   float red[128];
-  uint32_t xkey[2][4];
+  alignas(16) uint32_t xkey[2][4];
   float2 xval[2][4];
   int item;
+  TileDev T;
+  JobDev J;
 };
 constexpr size_t SMEM64 = sizeof(CtaSmem64);
 
 __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64& sm, int t) {
   const ClassArgs& C = a.c[CLS_F32_64];
   const int2 it = C.items[id];
-  const TileDev T = a.tiles[it.x];
-  const JobDev J = a.jobs[T.job];
+  copy_desc(&sm.T, a.tiles + it.x, t, 128);
+  __syncthreads();
+  copy_desc(&sm.J, a.jobs + sm.T.job, t, 128);
+  __syncthreads();
+  const TileDev& T = sm.T;
+  const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
   const int S = J.S, K = J.K;
   float* val = a.val_f + T.val_off;
@@ -504,22 +540,28 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, 128);
   __syncthreads();
   {
-    float2 x[64];
-    if (t < S) {  // row FFTs
+    // 64-point lines on lane pairs (l, l ^ 16): half h transforms the samples
+    // 2n + h (32 points), then X[k + 32h] = E[k] +- exp(-2 pi i k/64) O[k].
+    const int h = (t >> 4) & 1, line = ((t >> 5) << 4) | (t & 15);
+    float2 x[32];
+    if (line < S) {  // row FFTs (rows >= S are zero)
 #pragma unroll
-      for (int n = 0; n < 64; ++n) x[n] = n < S ? zbuf[swz<64>(t, n)] : make_float2(0.f, 0.f);
-      fft_reg<64>(x);
+      for (int n = 0; n < 32; ++n)
+        x[n] = 2 * n + h < S ? zbuf[swz<64>(line, 2 * n + h)] : make_float2(0.f, 0.f);
+      fft_reg<32>(x);
+      fft64_combine(x, h);
 #pragma unroll
-      for (int n = 0; n < 64; ++n) zbuf[swz<64>(t, n)] = x[n];
+      for (int k = 0; k < 32; ++k) zbuf[swz<64>(line, k + 32 * h)] = x[k];
     }
     __syncthreads();
-    if (t < 64) {  // column FFTs (in place, own column only)
+    // column FFTs: all 64 columns, own column only
 #pragma unroll
-      for (int m = 0; m < 64; ++m) x[m] = m < S ? zbuf[swz<64>(m, t)] : make_float2(0.f, 0.f);
-      fft_reg<64>(x);
+    for (int n = 0; n < 32; ++n)
+      x[n] = 2 * n + h < S ? zbuf[swz<64>(2 * n + h, line)] : make_float2(0.f, 0.f);
+    fft_reg<32>(x);
+    fft64_combine(x, h);
 #pragma unroll
-      for (int m = 0; m < 64; ++m) zbuf[swz<64>(m, t)] = x[m];
-    }
+    for (int k = 0; k < 32; ++k) zbuf[swz<64>(k + 32 * h, line)] = x[k];
     __syncthreads();
   }
   const int c = t & 63, hr = t >> 6, lane = t & 31, warp = t >> 5;
@@ -549,16 +591,15 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   const float gs = J.gamma_f / W0;
   const uint32_t tbits = (uint32_t)((1 - hr) << 11) | (uint32_t)(63 - c);
 
-  uint32_t best = 0;
+  uint32_t bq[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     const float e = fmaf(R[i].y, R[i].y, R[i].x * R[i].x);
-    best = max(best, (__float_as_uint(e) & 0xFFFFF000u) | (uint32_t)((31 - i) << 6));
+    bq[i & 3] = max(bq[i & 3], (__float_as_uint(e) & 0xFFFFF000u) | (uint32_t)((31 - i) << 6));
   }
-  best |= tbits;
+  uint32_t best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | tbits;
   for (int iter = 0; iter < K; ++iter) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, off));
+    best = __reduce_max_sync(0xffffffffu, best);
     {
       const int flat = 4095 - (int)(best & 4095u);
       const int i_w = (flat >> 6) & 31, l_w = flat & 31;
@@ -572,16 +613,12 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       }
     }
     __syncthreads();
-    uint32_t kb = sm.xkey[iter & 1][0];
-    int wb = 0;
-#pragma unroll
-    for (int w = 1; w < 4; ++w) {
-      const uint32_t kw = sm.xkey[iter & 1][w];
-      if (kw > kb) { kb = kw; wb = w; }
-    }
-    const float2 ru = sm.xval[iter & 1][wb];
+    const uint4 k4 = *reinterpret_cast<const uint4*>(sm.xkey[iter & 1]);
+    const uint32_t kb = max(max(k4.x, k4.y), max(k4.z, k4.w));
     const int flat = 4095 - (int)(kb & 4095u);
     const int u1 = flat >> 6, u2 = flat & 63;
+    // bin (u1, u2) lives in warp 2*(u1 >> 5) + (u2 >> 5)
+    const float2 ru = sm.xval[iter & 1][((u1 >> 5) << 1) | (u2 >> 5)];
     const float dx = gs * ru.x, dy = gs * ru.y;
     if (t == 0) {
       sm.coef_u[iter] = flat;
@@ -590,7 +627,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     }
     if (iter + 1 == K) break;
     const float2* wp = sm.Wd + (32 * hr - u1 + 64) * 64 + ((c - u2) & 63);
-    best = 0;
+    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       const float2 w = wp[i * 64];
@@ -600,9 +637,9 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       ry = fmaf(-dy, w.x, ry);
       R[i] = make_float2(rx, ry);
       const float e = fmaf(ry, ry, rx * rx);
-      best = max(best, (__float_as_uint(e) & 0xFFFFF000u) | (uint32_t)((31 - i) << 6));
+      bq[i & 3] = max(bq[i & 3], (__float_as_uint(e) & 0xFFFFF000u) | (uint32_t)((31 - i) << 6));
     }
-    best |= tbits;
+    best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | tbits;
   }
   __syncthreads();
   eval_and_write<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
@@ -638,9 +675,7 @@ __global__ void __launch_bounds__(128, 3) k_exec_f32_64(const __grid_constant__ 
     __threadfence();
     __syncthreads();
     const int2 it = C.items[id];
-    const TileDev T = a.tiles[it.x];
-    const JobDev J = a.jobs[T.job];
-    release_successors(a, C, T, J, it.y >> 16, it.y & 0xFFFF, t, 128);
+    release_successors(a, C, sm.T, sm.J, it.y >> 16, it.y & 0xFFFF, t, 128);
     if (t == 0) atomicAdd(&C.q->n_done, 1);
     __syncthreads();
   }
