@@ -544,14 +544,20 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     // 2n + h (32 points), then X[k + 32h] = E[k] +- exp(-2 pi i k/64) O[k].
     const int h = (t >> 4) & 1, line = ((t >> 5) << 4) | (t & 15);
     float2 x[32];
-    if (line < S) {  // row FFTs (rows >= S are zero)
+    // row FFTs (rows >= S are zero).  The branch is warp-uniform: the pair
+    // combine shuffles across the whole warp, so every lane of a warp that
+    // holds any row < S takes part; lanes past S only skip loads and stores.
+    if (((t >> 5) << 4) < S) {
+      const bool live = line < S;
 #pragma unroll
       for (int n = 0; n < 32; ++n)
-        x[n] = 2 * n + h < S ? zbuf[swz<64>(line, 2 * n + h)] : make_float2(0.f, 0.f);
+        x[n] = live && 2 * n + h < S ? zbuf[swz<64>(live ? line : 0, 2 * n + h)] : make_float2(0.f, 0.f);
       fft_reg<32>(x);
       fft64_combine(x, h);
+      if (live) {
 #pragma unroll
-      for (int k = 0; k < 32; ++k) zbuf[swz<64>(line, k + 32 * h)] = x[k];
+        for (int k = 0; k < 32; ++k) zbuf[swz<64>(line, k + 32 * h)] = x[k];
+      }
     }
     __syncthreads();
     // column FFTs: all 64 columns, own column only
