@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--arena-mb", type=int, default=4096)
+    ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 4, 8])
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
     return ap.parse_args()
 
 
@@ -195,6 +197,10 @@ def main():
     dev = torch.device("cuda", local)
     ctx = fse.Context(local, arena_bytes=args.arena_mb << 20)
     ctx.exec_mode(args.mode)
+    if args.f64_warps:
+        ctx.set_option(fse.OPT_F64_WARPS, args.f64_warps)
+    if args.ctas_per_sm:
+        ctx.set_option(fse.OPT_CTAS_PER_SM, args.ctas_per_sm)
     keep, cjobs, pix = [], [], 0
     for j in jobs:
         img = torch.from_numpy(j["image"]).to(dev)
@@ -304,7 +310,7 @@ def main():
     if rank == 0:
         cfg = describe(args.workload, jobs)
         cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                    "exec_mode": args.mode, "l2": "flushed between steps (256 MB write)",
+                    "exec_mode": args.mode, "f64_warps": args.f64_warps or 4, "l2": "flushed between steps (256 MB write)",
                     "lost_blocks_per_step": blocks, "core_lost_blocks_per_step": core_blocks,
                     "bin_iterations_per_step": bins})
         line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,

@@ -72,6 +72,17 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
     case FSE_OPT_DEBUG_CAPTURE:
       c->debug = value != 0;
       return FSE_OK;
+    case FSE_OPT_F64_WARPS: {
+      if (value != 0 && value != 4 && value != 8) return fse::fail(FSE_EINVAL, "f64 warps");
+      fse::set_f64_warps(value == 0 ? 4 : (int)value);
+      int nb = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fse::exec_kernel_ptr(fse::CLS_F32_64),
+                                                    fse::exec_threads(fse::CLS_F32_64),
+                                                    fse::exec_smem(fse::CLS_F32_64));
+      c->occupancy[fse::CLS_F32_64] = nb > 0 ? nb : 1;
+      c->graph_jobs.clear();
+      return FSE_OK;
+    }
     case FSE_OPT_KERNEL_TIMING:
       c->kernel_timing = value != 0;
       c->tev_used = 0;

@@ -99,6 +99,8 @@ cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st);
 cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st);
 cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st);
 int exec_threads(int cls);
+void set_f64_warps(int nwb);  // warps per block of the F = 64 executor (4 or 8)
+int get_f64_warps();
 size_t exec_smem(int cls);
 cudaError_t exec_setup(int device);  // smem opt-in for every executor kernel
 const void* exec_kernel_ptr(int cls);

@@ -344,6 +344,35 @@ __device__ __forceinline__ void debug_useq(const ExecArgs& a, int cls, int id, i
     case 30: v = R[30]; break; default: v = R[31]; break;              \
   }
 
+// Register select R[i] for a warp-uniform i < N (branch tree, no local memory).
+template <int N>
+__device__ __forceinline__ float2 select_reg(const float2 (&R)[N], int i) {
+  float2 v;
+  if constexpr (N == 32) {
+    FSE_SEL32(R, i, v);
+  } else {
+    switch (i) {
+      case 0: v = R[0]; break;   case 1: v = R[1]; break;
+      case 2: v = R[2]; break;   case 3: v = R[3]; break;
+      case 4: v = R[4]; break;   case 5: v = R[5]; break;
+      case 6: v = R[6]; break;   case 7: v = R[7]; break;
+      case 8: v = R[8]; break;   case 9: v = R[9]; break;
+      case 10: v = R[10]; break; case 11: v = R[11]; break;
+      case 12: v = R[12]; break; case 13: v = R[13]; break;
+      case 14: v = R[14]; break; default: v = R[15]; break;
+    }
+  }
+  return v;
+}
+
+// An opaque register copy of a constant, so that "(bits & m) | imm" stays a
+// single three-input logic op instead of two immediate ones.
+__device__ __forceinline__ uint32_t opaque(uint32_t v) {
+  uint32_t r;
+  asm volatile("mov.b32 %0, %1;" : "=r"(r) : "r"(v));
+  return r;
+}
+
 // ===========================================================================
 // Executor 1: FP32, F = 32.  One warp per lost block.  Lane l owns spectrum
 // column k2 = l, bins (k1 = j, l) for j = 0..31 in registers.  W sits in
@@ -426,19 +455,19 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
   const float gs = J.gamma_f / W0;
   float2(&R)[32] = x;
 
+  const uint32_t kmask = opaque(0xFFFFFC00u);
   uint32_t bq[4] = {0u, 0u, 0u, 0u};  // four independent max chains
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const float e = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
-    bq[j & 3] = max(bq[j & 3], (__float_as_uint(e) & 0xFFFFFC00u) | (uint32_t)((31 - j) << 5));
+    bq[j & 3] = max(bq[j & 3], (__float_as_uint(e) & kmask) | (uint32_t)((31 - j) << 5));
   }
   uint32_t best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | (uint32_t)(31 - lane);
   for (int iter = 0; iter < K; ++iter) {
     best = __reduce_max_sync(0xffffffffu, best);
     const int flat = 1023 - (int)(best & 1023u);
     const int u1 = flat >> 5, u2 = flat & 31;
-    float2 v;
-    FSE_SEL32(R, u1, v);
+    const float2 v = select_reg<32>(R, u1);
     const float rux = __shfl_sync(0xffffffffu, v.x, u2);
     const float ruy = __shfl_sync(0xffffffffu, v.y, u2);
     const float dx = gs * rux, dy = gs * ruy;
@@ -459,7 +488,7 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
       ry = fmaf(-dy, w.x, ry);
       R[j] = make_float2(rx, ry);
       const float e = fmaf(ry, ry, rx * rx);
-      bq[j & 3] = max(bq[j & 3], (__float_as_uint(e) & 0xFFFFFC00u) | (uint32_t)((31 - j) << 5));
+      bq[j & 3] = max(bq[j & 3], (__float_as_uint(e) & kmask) | (uint32_t)((31 - j) << 5));
     }
     best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | (uint32_t)(31 - lane);
   }
@@ -503,31 +532,34 @@ __global__ void __launch_bounds__(NW32 * 32, 5) k_exec_f32_32(const __grid_const
 }
 
 // ===========================================================================
-// Executor 2: FP32, F = 64.  Four warps (128 threads) per lost block.  Thread
-// t owns column c = t & 63 and rows k1 = i + 32*(t >> 6), i = 0..31, in
-// registers.  Per iteration: warp argmax, then a 4-way exchange through
-// shared memory behind one barrier (double-buffered by iteration parity).
+// Executor 2: FP32, F = 64.  NWB warps (NT = 32*NWB threads) per lost block.
+// Thread t owns spectrum column c = t & 63 and rows k1 = i + RPT*(t >> 6),
+// i = 0..RPT-1 (RPT = 4096 / NT), in registers.  Per iteration: warp max
+// (redux), then an NWB-way exchange through shared memory behind one
+// barrier, double-buffered by iteration parity.
 // ===========================================================================
+template <int NWB>
 struct alignas(16) CtaSmem64 {
   float2 Wd[128 * 64];   // rows 0..127: W rows (r mod 64); 64..127 double as FFT buffer
   float2 coef_d[KMAX];
   int32_t coef_u[KMAX];
   float2 tw[64];
-  float red[128];
-  alignas(16) uint32_t xkey[2][4];
-  float2 xval[2][4];
+  float red[NWB * 32];
+  alignas(16) uint32_t xkey[2][NWB];
+  float2 xval[2][NWB];
   int item;
   TileDev T;
   JobDev J;
 };
-constexpr size_t SMEM64 = sizeof(CtaSmem64);
 
-__device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64& sm, int t) {
+template <int NWB>
+__device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64<NWB>& sm, int t) {
+  constexpr int NT = NWB * 32, RPT = 4096 / NT, NQ = NT / 64;
   const ClassArgs& C = a.c[CLS_F32_64];
   const int2 it = C.items[id];
-  copy_desc(&sm.T, a.tiles + it.x, t, 128);
+  copy_desc(&sm.T, a.tiles + it.x, t, NT);
   __syncthreads();
-  copy_desc(&sm.J, a.jobs + sm.T.job, t, 128);
+  copy_desc(&sm.J, a.jobs + sm.T.job, t, NT);
   __syncthreads();
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -537,9 +569,9 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   if (t == 0) debug_record(a, CLS_F32_64, id, T, it.x, I, Jb);
   float2* zbuf = sm.Wd + 64 * 64;
 
-  stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, 128);
+  stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, NT);
   __syncthreads();
-  {
+  if (t < 128) {
     // 64-point lines on lane pairs (l, l ^ 16): half h transforms the samples
     // 2n + h (32 points), then X[k + 32h] = E[k] +- exp(-2 pi i k/64) O[k].
     const int h = (t >> 4) & 1, line = ((t >> 5) << 4) | (t & 15);
@@ -559,8 +591,12 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
         for (int k = 0; k < 32; ++k) zbuf[swz<64>(line, k + 32 * h)] = x[k];
       }
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (t < 128) {
     // column FFTs: all 64 columns, own column only
+    const int h = (t >> 4) & 1, line = ((t >> 5) << 4) | (t & 15);
+    float2 x[32];
 #pragma unroll
     for (int n = 0; n < 32; ++n)
       x[n] = 2 * n + h < S ? zbuf[swz<64>(2 * n + h, line)] : make_float2(0.f, 0.f);
@@ -568,15 +604,15 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     fft64_combine(x, h);
 #pragma unroll
     for (int k = 0; k < 32; ++k) zbuf[swz<64>(k + 32 * h, line)] = x[k];
-    __syncthreads();
   }
-  const int c = t & 63, hr = t >> 6, lane = t & 31, warp = t >> 5;
-  float2 R[32];
+  __syncthreads();
+  const int c = t & 63, q = t >> 6, lane = t & 31, warp = t >> 5;
+  float2 R[RPT];
   {
     const int cm = (64 - c) & 63;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const int k1 = i + 32 * hr, k1m = (64 - k1) & 63;
+    for (int i = 0; i < RPT; ++i) {
+      const int k1 = i + RPT * q, k1m = (64 - k1) & 63;
       const float2 z = zbuf[swz<64>(k1, c)], zm = zbuf[swz<64>(k1m, cm)];
       sm.Wd[k1 * 64 + c] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
       R[i] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
@@ -584,8 +620,8 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int k1 = i + 32 * hr;
+  for (int i = 0; i < RPT; ++i) {
+    const int k1 = i + RPT * q;
     sm.Wd[(k1 + 64) * 64 + c] = sm.Wd[k1 * 64 + c];
   }
   __syncthreads();
@@ -595,22 +631,23 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     return;
   }
   const float gs = J.gamma_f / W0;
-  const uint32_t tbits = (uint32_t)((1 - hr) << 11) | (uint32_t)(63 - c);
+  // key = energy bits, low 12 bits replaced by 4095 - flat; flat = k1*64 + c
+  const uint32_t kmask = opaque(0xFFFFF000u);
+  const uint32_t tbits = (uint32_t)(((NQ - 1 - q) * RPT) << 6) | (uint32_t)(63 - c);
 
   uint32_t bq[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
+  for (int i = 0; i < RPT; ++i) {
     const float e = fmaf(R[i].y, R[i].y, R[i].x * R[i].x);
-    bq[i & 3] = max(bq[i & 3], (__float_as_uint(e) & 0xFFFFF000u) | (uint32_t)((31 - i) << 6));
+    bq[i & 3] = max(bq[i & 3], (__float_as_uint(e) & kmask) | (uint32_t)((RPT - 1 - i) << 6));
   }
   uint32_t best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | tbits;
   for (int iter = 0; iter < K; ++iter) {
     best = __reduce_max_sync(0xffffffffu, best);
     {
       const int flat = 4095 - (int)(best & 4095u);
-      const int i_w = (flat >> 6) & 31, l_w = flat & 31;
-      float2 v;
-      FSE_SEL32(R, i_w, v);
+      const int i_w = (flat >> 6) % RPT, l_w = flat & 31;
+      float2 v = select_reg<RPT>(R, i_w);
       v.x = __shfl_sync(0xffffffffu, v.x, l_w);
       v.y = __shfl_sync(0xffffffffu, v.y, l_w);
       if (lane == 0) {
@@ -619,12 +656,19 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       }
     }
     __syncthreads();
-    const uint4 k4 = *reinterpret_cast<const uint4*>(sm.xkey[iter & 1]);
-    const uint32_t kb = max(max(k4.x, k4.y), max(k4.z, k4.w));
+    uint32_t kb;
+    if constexpr (NWB == 4) {
+      const uint4 k4 = *reinterpret_cast<const uint4*>(sm.xkey[iter & 1]);
+      kb = max(max(k4.x, k4.y), max(k4.z, k4.w));
+    } else {
+      const uint4 k4 = *reinterpret_cast<const uint4*>(sm.xkey[iter & 1]);
+      const uint4 k5 = *reinterpret_cast<const uint4*>(sm.xkey[iter & 1] + 4);
+      kb = max(max(max(k4.x, k4.y), max(k4.z, k4.w)), max(max(k5.x, k5.y), max(k5.z, k5.w)));
+    }
     const int flat = 4095 - (int)(kb & 4095u);
     const int u1 = flat >> 6, u2 = flat & 63;
-    // bin (u1, u2) lives in warp 2*(u1 >> 5) + (u2 >> 5)
-    const float2 ru = sm.xval[iter & 1][((u1 >> 5) << 1) | (u2 >> 5)];
+    // bin (u1, u2) lives in warp 2*(u1 / RPT) + (u2 >> 5)
+    const float2 ru = sm.xval[iter & 1][((u1 / RPT) << 1) | (u2 >> 5)];
     const float dx = gs * ru.x, dy = gs * ru.y;
     if (t == 0) {
       sm.coef_u[iter] = flat;
@@ -632,10 +676,10 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       debug_useq(a, CLS_F32_64, id, iter, flat);
     }
     if (iter + 1 == K) break;
-    const float2* wp = sm.Wd + (32 * hr - u1 + 64) * 64 + ((c - u2) & 63);
+    const float2* wp = sm.Wd + (RPT * q - u1 + 64) * 64 + ((c - u2) & 63);
     bq[0] = bq[1] = bq[2] = bq[3] = 0u;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
+    for (int i = 0; i < RPT; ++i) {
       const float2 w = wp[i * 64];
       float rx = fmaf(-dx, w.x, R[i].x);
       rx = fmaf(dy, w.y, rx);
@@ -643,31 +687,33 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       ry = fmaf(-dy, w.x, ry);
       R[i] = make_float2(rx, ry);
       const float e = fmaf(ry, ry, rx * rx);
-      bq[i & 3] = max(bq[i & 3], (__float_as_uint(e) & 0xFFFFF000u) | (uint32_t)((31 - i) << 6));
+      bq[i & 3] = max(bq[i & 3], (__float_as_uint(e) & kmask) | (uint32_t)((RPT - 1 - i) << 6));
     }
     best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | tbits;
   }
   __syncthreads();
   eval_and_write<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
-                                      128);
+                                      NT);
 }
 
-__global__ void __launch_bounds__(128, 3) k_exec_f32_64(const __grid_constant__ ExecArgs a) {
+template <int NWB>
+__global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : 3) k_exec_f32_64(const __grid_constant__ ExecArgs a) {
+  constexpr int NT = NWB * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CtaSmem64& sm = *reinterpret_cast<CtaSmem64*>(smem_raw);
+  CtaSmem64<NWB>& sm = *reinterpret_cast<CtaSmem64<NWB>*>(smem_raw);
   const int t = threadIdx.x;
   if (t < 64) sm.tw[t] = make_float2(c_twf[t].x, -c_twf[t].y);
   __syncthreads();
   const ClassArgs& C = a.c[CLS_F32_64];
   if (a.single_item >= 0) {
-    if (blockIdx.x == 0) item_f32_64(a, a.single_item, sm, t);
+    if (blockIdx.x == 0) item_f32_64<NWB>(a, a.single_item, sm, t);
     return;
   }
   if (a.level_mode) {
     const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x; id < n; id += gridDim.x)
       if (a.level_of[(size_t)CLS_F32_64 * a.level_stride + id] == a.level) {
-        item_f32_64(a, id, sm, t);
+        item_f32_64<NWB>(a, id, sm, t);
         __syncthreads();
       }
     return;
@@ -677,11 +723,11 @@ __global__ void __launch_bounds__(128, 3) k_exec_f32_64(const __grid_constant__ 
     __syncthreads();
     const int id = sm.item;
     if (id < 0) break;
-    item_f32_64(a, id, sm, t);
+    item_f32_64<NWB>(a, id, sm, t);
     __threadfence();
     __syncthreads();
     const int2 it = C.items[id];
-    release_successors(a, C, sm.T, sm.J, it.y >> 16, it.y & 0xFFFF, t, 128);
+    release_successors(a, C, sm.T, sm.J, it.y >> 16, it.y & 0xFFFF, t, NT);
     if (t == 0) atomicAdd(&C.q->n_done, 1);
     __syncthreads();
   }
@@ -959,18 +1005,33 @@ __global__ void k_probe(const __grid_constant__ ExecArgs a) {
 // ===========================================================================
 // launchers
 // ===========================================================================
-int exec_threads(int cls) { return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? 128 : NT64); }
-size_t exec_smem(int cls) { return cls == CLS_F32_32 ? SMEM32 : (cls == CLS_F32_64 ? SMEM64 : SMEMD); }
+int g_nwb64 = 4;  // warps per block of the F = 64 executor (4 or 8)
+void set_f64_warps(int nwb) { g_nwb64 = nwb == 8 ? 8 : 4; }
+int get_f64_warps() { return g_nwb64; }
+int exec_threads(int cls) {
+  return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? g_nwb64 * 32 : NT64);
+}
+size_t exec_smem(int cls) {
+  if (cls == CLS_F32_32) return SMEM32;
+  if (cls == CLS_F32_64) return g_nwb64 == 8 ? sizeof(CtaSmem64<8>) : sizeof(CtaSmem64<4>);
+  return SMEMD;
+}
 const void* exec_kernel_ptr(int cls) {
-  return cls == CLS_F32_32 ? (const void*)k_exec_f32_32
-                           : (cls == CLS_F32_64 ? (const void*)k_exec_f32_64 : (const void*)k_exec_f64);
+  if (cls == CLS_F32_32) return (const void*)k_exec_f32_32;
+  if (cls == CLS_F32_64)
+    return g_nwb64 == 8 ? (const void*)k_exec_f32_64<8> : (const void*)k_exec_f32_64<4>;
+  return (const void*)k_exec_f64;
 }
 
 cudaError_t exec_setup(int device) {
   (void)device;
   cudaError_t e = cudaFuncSetAttribute(k_exec_f32_32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM32);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_exec_f32_64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM64);
+  e = cudaFuncSetAttribute(k_exec_f32_64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(CtaSmem64<4>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_exec_f32_64<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(CtaSmem64<8>));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_exec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEMD);
 }
@@ -998,7 +1059,10 @@ cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st) {
 cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
   if (cls == CLS_F32_32) k_exec_f32_32<<<grid, NW32 * 32, SMEM32, st>>>(a);
-  else if (cls == CLS_F32_64) k_exec_f32_64<<<grid, 128, SMEM64, st>>>(a);
+  else if (cls == CLS_F32_64 && g_nwb64 == 8)
+    k_exec_f32_64<8><<<grid, 256, sizeof(CtaSmem64<8>), st>>>(a);
+  else if (cls == CLS_F32_64)
+    k_exec_f32_64<4><<<grid, 128, sizeof(CtaSmem64<4>), st>>>(a);
   else k_exec_f64<<<grid, NT64, SMEMD, st>>>(a);
   return cudaGetLastError();
 }
