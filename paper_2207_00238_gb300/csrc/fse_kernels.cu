@@ -145,22 +145,24 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
     wiso = J.wiso_d;
     delta = J.delta;
   }
+  const bool use_done = J.order != ORDER_INDEPENDENT;
   for (int e = t; e < S * S; e += nthr) {
     const int m = e / S, n = e - m * S;
     real wv = 0, zr = 0;
     const int ty = oy + m, tx = ox + n;
     if (ty >= 0 && ty < T.eh && tx >= 0 && tx < T.ew) {
+      // independent loads first (mask, pixel, value plane), then combine
       const size_t gi = (size_t)(T.ey + ty) * J.pitch + (T.ex + tx);
       const real wi = __ldg(wiso + e);
-      if (__ldg(J.mask + gi) == 0) {
+      const uint8_t mk = __ldg(J.mask + gi);
+      const real px = (real)__ldg(J.image + gi);
+      const real v = __ldcg(val + (size_t)ty * T.ew + tx);
+      if (mk == 0) {
         wv = wi;
-        zr = wi * (real)__ldg(J.image + gi);
-      } else if (J.order != ORDER_INDEPENDENT) {
-        const real v = __ldcg(val + (size_t)ty * T.ew + tx);
-        if (!isnan(v)) {
-          wv = delta * wi;
-          zr = wv * v;
-        }
+        zr = wi * px;
+      } else if (use_done && !isnan(v)) {
+        wv = delta * wi;
+        zr = wv * v;
       }
     }
     real2 z;
@@ -348,7 +350,15 @@ __device__ __forceinline__ void debug_useq(const ExecArgs& a, int cls, int id, i
 template <int N>
 __device__ __forceinline__ float2 select_reg(const float2 (&R)[N], int i) {
   float2 v;
-  if constexpr (N == 32) {
+  if constexpr (N == 64) {
+    if (i < 32) {
+      const float2(&lo)[32] = *reinterpret_cast<const float2(*)[32]>(&R[0]);
+      FSE_SEL32(lo, i, v);
+    } else {
+      const float2(&hi)[32] = *reinterpret_cast<const float2(*)[32]>(&R[32]);
+      FSE_SEL32(hi, i - 32, v);
+    }
+  } else if constexpr (N == 32) {
     FSE_SEL32(R, i, v);
   } else {
     switch (i) {
@@ -545,8 +555,7 @@ struct alignas(16) CtaSmem64 {
   int32_t coef_u[KMAX];
   float2 tw[64];
   float red[NWB * 32];
-  alignas(16) uint32_t xkey[2][NWB];
-  float2 xval[2][NWB];
+  alignas(16) float4 xrec[2][NWB];  // per warp: (key bits, 0, Re R_u, Im R_u)
   int item;
   TileDev T;
   JobDev J;
@@ -571,15 +580,16 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
 
   stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, NT);
   __syncthreads();
-  if (t < 128) {
-    // 64-point lines on lane pairs (l, l ^ 16): half h transforms the samples
-    // 2n + h (32 points), then X[k + 32h] = E[k] +- exp(-2 pi i k/64) O[k].
-    const int h = (t >> 4) & 1, line = ((t >> 5) << 4) | (t & 15);
+  // 64-point lines on lane pairs (l, l ^ 16): half h transforms the samples
+  // 2n + h (32 points), then X[k + 32h] = E[k] +- exp(-2 pi i k/64) O[k].
+  // NT/2 lines per pass.
+  for (int lb = 0; lb < 64; lb += NT / 2) {
+    const int h = (t >> 4) & 1, line = lb + (((t >> 5) << 4) | (t & 15));
     float2 x[32];
     // row FFTs (rows >= S are zero).  The branch is warp-uniform: the pair
     // combine shuffles across the whole warp, so every lane of a warp that
     // holds any row < S takes part; lanes past S only skip loads and stores.
-    if (((t >> 5) << 4) < S) {
+    if (t < 128 && lb + ((t >> 5) << 4) < S) {
       const bool live = line < S;
 #pragma unroll
       for (int n = 0; n < 32; ++n)
@@ -593,17 +603,19 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     }
   }
   __syncthreads();
-  if (t < 128) {
-    // column FFTs: all 64 columns, own column only
-    const int h = (t >> 4) & 1, line = ((t >> 5) << 4) | (t & 15);
-    float2 x[32];
+  for (int lb = 0; lb < 64; lb += NT / 2) {
+    if (t < 128) {
+      // column FFTs: own column only
+      const int h = (t >> 4) & 1, line = lb + (((t >> 5) << 4) | (t & 15));
+      float2 x[32];
 #pragma unroll
-    for (int n = 0; n < 32; ++n)
-      x[n] = 2 * n + h < S ? zbuf[swz<64>(2 * n + h, line)] : make_float2(0.f, 0.f);
-    fft_reg<32>(x);
-    fft64_combine(x, h);
+      for (int n = 0; n < 32; ++n)
+        x[n] = 2 * n + h < S ? zbuf[swz<64>(2 * n + h, line)] : make_float2(0.f, 0.f);
+      fft_reg<32>(x);
+      fft64_combine(x, h);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) zbuf[swz<64>(k + 32 * h, line)] = x[k];
+      for (int k = 0; k < 32; ++k) zbuf[swz<64>(k + 32 * h, line)] = x[k];
+    }
   }
   __syncthreads();
   const int c = t & 63, q = t >> 6, lane = t & 31, warp = t >> 5;
@@ -650,25 +662,20 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       float2 v = select_reg<RPT>(R, i_w);
       v.x = __shfl_sync(0xffffffffu, v.x, l_w);
       v.y = __shfl_sync(0xffffffffu, v.y, l_w);
-      if (lane == 0) {
-        sm.xkey[iter & 1][warp] = best;
-        sm.xval[iter & 1][warp] = v;
-      }
+      if (lane == 0) sm.xrec[iter & 1][warp] = make_float4(__uint_as_float(best), 0.f, v.x, v.y);
     }
     __syncthreads();
-    uint32_t kb;
-    if constexpr (NWB == 4) {
-      const uint4 k4 = *reinterpret_cast<const uint4*>(sm.xkey[iter & 1]);
-      kb = max(max(k4.x, k4.y), max(k4.z, k4.w));
-    } else {
-      const uint4 k4 = *reinterpret_cast<const uint4*>(sm.xkey[iter & 1]);
-      const uint4 k5 = *reinterpret_cast<const uint4*>(sm.xkey[iter & 1] + 4);
-      kb = max(max(max(k4.x, k4.y), max(k4.z, k4.w)), max(max(k5.x, k5.y), max(k5.z, k5.w)));
+    // largest key over the warps, carrying its R_u (one shared-memory round trip)
+    float4 rb = sm.xrec[iter & 1][0];
+#pragma unroll
+    for (int w = 1; w < NWB; ++w) {
+      const float4 rw = sm.xrec[iter & 1][w];
+      if (__float_as_uint(rw.x) > __float_as_uint(rb.x)) rb = rw;
     }
+    const uint32_t kb = __float_as_uint(rb.x);
     const int flat = 4095 - (int)(kb & 4095u);
     const int u1 = flat >> 6, u2 = flat & 63;
-    // bin (u1, u2) lives in warp 2*(u1 / RPT) + (u2 >> 5)
-    const float2 ru = sm.xval[iter & 1][((u1 / RPT) << 1) | (u2 >> 5)];
+    const float2 ru = make_float2(rb.z, rb.w);
     const float dx = gs * ru.x, dy = gs * ru.y;
     if (t == 0) {
       sm.coef_u[iter] = flat;
@@ -697,7 +704,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
 }
 
 template <int NWB>
-__global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : 3) k_exec_f32_64(const __grid_constant__ ExecArgs a) {
+__global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : 3)) k_exec_f32_64(const __grid_constant__ ExecArgs a) {
   constexpr int NT = NWB * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CtaSmem64<NWB>& sm = *reinterpret_cast<CtaSmem64<NWB>*>(smem_raw);
@@ -1006,20 +1013,22 @@ __global__ void k_probe(const __grid_constant__ ExecArgs a) {
 // launchers
 // ===========================================================================
 int g_nwb64 = 4;  // warps per block of the F = 64 executor (4 or 8)
-void set_f64_warps(int nwb) { g_nwb64 = nwb == 8 ? 8 : 4; }
+void set_f64_warps(int nwb) { g_nwb64 = (nwb == 8 || nwb == 2) ? nwb : 4; }
 int get_f64_warps() { return g_nwb64; }
 int exec_threads(int cls) {
   return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? g_nwb64 * 32 : NT64);
 }
 size_t exec_smem(int cls) {
   if (cls == CLS_F32_32) return SMEM32;
-  if (cls == CLS_F32_64) return g_nwb64 == 8 ? sizeof(CtaSmem64<8>) : sizeof(CtaSmem64<4>);
+  if (cls == CLS_F32_64)
+    return g_nwb64 == 8 ? sizeof(CtaSmem64<8>) : (g_nwb64 == 2 ? sizeof(CtaSmem64<2>) : sizeof(CtaSmem64<4>));
   return SMEMD;
 }
 const void* exec_kernel_ptr(int cls) {
   if (cls == CLS_F32_32) return (const void*)k_exec_f32_32;
   if (cls == CLS_F32_64)
-    return g_nwb64 == 8 ? (const void*)k_exec_f32_64<8> : (const void*)k_exec_f32_64<4>;
+    return g_nwb64 == 8 ? (const void*)k_exec_f32_64<8>
+                        : (g_nwb64 == 2 ? (const void*)k_exec_f32_64<2> : (const void*)k_exec_f32_64<4>);
   return (const void*)k_exec_f64;
 }
 
@@ -1032,6 +1041,9 @@ cudaError_t exec_setup(int device) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_exec_f32_64<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(CtaSmem64<8>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_exec_f32_64<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(CtaSmem64<2>));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_exec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEMD);
 }
@@ -1061,6 +1073,8 @@ cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st) {
   if (cls == CLS_F32_32) k_exec_f32_32<<<grid, NW32 * 32, SMEM32, st>>>(a);
   else if (cls == CLS_F32_64 && g_nwb64 == 8)
     k_exec_f32_64<8><<<grid, 256, sizeof(CtaSmem64<8>), st>>>(a);
+  else if (cls == CLS_F32_64 && g_nwb64 == 2)
+    k_exec_f32_64<2><<<grid, 64, sizeof(CtaSmem64<2>), st>>>(a);
   else if (cls == CLS_F32_64)
     k_exec_f32_64<4><<<grid, 128, sizeof(CtaSmem64<4>), st>>>(a);
   else k_exec_f64<<<grid, NT64, SMEMD, st>>>(a);

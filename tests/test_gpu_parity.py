@@ -87,6 +87,18 @@ def _seq_check(oracle_lib, ctx, job, **over):
     assert (got[0]["out"] == ref["out"]).all()
 
 
+@pytest.mark.parametrize("warps", [2, 4, 8])
+def test_fp32_f64_executor_variants(ctx, oracle_lib, warps):
+    """Each warps-per-block variant of the F = 64 executor meets the FP32 gate."""
+    job = _small_tiled()
+    ctx.set_option(fse.OPT_F64_WARPS, warps)
+    try:
+        got, _ = run_gpu(ctx, [job])
+    finally:
+        ctx.set_option(fse.OPT_F64_WARPS, 0)
+    _fp32_check(oracle_lib, job, got[0])
+
+
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_fp64_selection_sequence(ctx, oracle_lib, case):
     _seq_check(oracle_lib, ctx, CASES[case]())
