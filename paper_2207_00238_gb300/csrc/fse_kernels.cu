@@ -326,53 +326,105 @@ __device__ __forceinline__ void debug_useq(const ExecArgs& a, int cls, int id, i
 // 12 (F = 64) mantissa bits replaced by the inverted flat index, so that an
 // integer max picks the largest energy and, among energies equal to the
 // kept precision, the lowest flat index k1*F + k2.
-#define FSE_SEL32(R, j, v)                                              \
-  switch (j) {                                                         \
-    case 0: v = R[0]; break;   case 1: v = R[1]; break;                \
-    case 2: v = R[2]; break;   case 3: v = R[3]; break;                \
-    case 4: v = R[4]; break;   case 5: v = R[5]; break;                \
-    case 6: v = R[6]; break;   case 7: v = R[7]; break;                \
-    case 8: v = R[8]; break;   case 9: v = R[9]; break;                \
-    case 10: v = R[10]; break; case 11: v = R[11]; break;              \
-    case 12: v = R[12]; break; case 13: v = R[13]; break;              \
-    case 14: v = R[14]; break; case 15: v = R[15]; break;              \
-    case 16: v = R[16]; break; case 17: v = R[17]; break;              \
-    case 18: v = R[18]; break; case 19: v = R[19]; break;              \
-    case 20: v = R[20]; break; case 21: v = R[21]; break;              \
-    case 22: v = R[22]; break; case 23: v = R[23]; break;              \
-    case 24: v = R[24]; break; case 25: v = R[25]; break;              \
-    case 26: v = R[26]; break; case 27: v = R[27]; break;              \
-    case 28: v = R[28]; break; case 29: v = R[29]; break;              \
-    case 30: v = R[30]; break; default: v = R[31]; break;              \
-  }
 
-// Register select R[i] for a warp-uniform i < N (branch tree, no local memory).
+// Register select v = R[i] for a warp-uniform i: one indirect branch through a
+// jump table (brx.idx) to a pair of moves, so the spectrum stays in registers
+// and the select costs one branch instead of a compare tree.
+__device__ __forceinline__ float2 select_reg32(const float2 (&R)[32], int i) {
+  float vx, vy;
+  asm volatile(
+      "{\n"
+      "ts: .branchtargets L0, L1, L2, L3, L4, L5, L6, L7, L8, L9, L10, L11, L12, L13, L14, L15, L16, L17, L18, L19, L20, L21, L22, L23, L24, L25, L26, L27, L28, L29, L30, L31;\n"
+      "brx.idx.uni %2, ts;\n"
+      "L0: mov.b32 %0, %3; mov.b32 %1, %4; bra.uni LEND;\n"
+      "L1: mov.b32 %0, %5; mov.b32 %1, %6; bra.uni LEND;\n"
+      "L2: mov.b32 %0, %7; mov.b32 %1, %8; bra.uni LEND;\n"
+      "L3: mov.b32 %0, %9; mov.b32 %1, %10; bra.uni LEND;\n"
+      "L4: mov.b32 %0, %11; mov.b32 %1, %12; bra.uni LEND;\n"
+      "L5: mov.b32 %0, %13; mov.b32 %1, %14; bra.uni LEND;\n"
+      "L6: mov.b32 %0, %15; mov.b32 %1, %16; bra.uni LEND;\n"
+      "L7: mov.b32 %0, %17; mov.b32 %1, %18; bra.uni LEND;\n"
+      "L8: mov.b32 %0, %19; mov.b32 %1, %20; bra.uni LEND;\n"
+      "L9: mov.b32 %0, %21; mov.b32 %1, %22; bra.uni LEND;\n"
+      "L10: mov.b32 %0, %23; mov.b32 %1, %24; bra.uni LEND;\n"
+      "L11: mov.b32 %0, %25; mov.b32 %1, %26; bra.uni LEND;\n"
+      "L12: mov.b32 %0, %27; mov.b32 %1, %28; bra.uni LEND;\n"
+      "L13: mov.b32 %0, %29; mov.b32 %1, %30; bra.uni LEND;\n"
+      "L14: mov.b32 %0, %31; mov.b32 %1, %32; bra.uni LEND;\n"
+      "L15: mov.b32 %0, %33; mov.b32 %1, %34; bra.uni LEND;\n"
+      "L16: mov.b32 %0, %35; mov.b32 %1, %36; bra.uni LEND;\n"
+      "L17: mov.b32 %0, %37; mov.b32 %1, %38; bra.uni LEND;\n"
+      "L18: mov.b32 %0, %39; mov.b32 %1, %40; bra.uni LEND;\n"
+      "L19: mov.b32 %0, %41; mov.b32 %1, %42; bra.uni LEND;\n"
+      "L20: mov.b32 %0, %43; mov.b32 %1, %44; bra.uni LEND;\n"
+      "L21: mov.b32 %0, %45; mov.b32 %1, %46; bra.uni LEND;\n"
+      "L22: mov.b32 %0, %47; mov.b32 %1, %48; bra.uni LEND;\n"
+      "L23: mov.b32 %0, %49; mov.b32 %1, %50; bra.uni LEND;\n"
+      "L24: mov.b32 %0, %51; mov.b32 %1, %52; bra.uni LEND;\n"
+      "L25: mov.b32 %0, %53; mov.b32 %1, %54; bra.uni LEND;\n"
+      "L26: mov.b32 %0, %55; mov.b32 %1, %56; bra.uni LEND;\n"
+      "L27: mov.b32 %0, %57; mov.b32 %1, %58; bra.uni LEND;\n"
+      "L28: mov.b32 %0, %59; mov.b32 %1, %60; bra.uni LEND;\n"
+      "L29: mov.b32 %0, %61; mov.b32 %1, %62; bra.uni LEND;\n"
+      "L30: mov.b32 %0, %63; mov.b32 %1, %64; bra.uni LEND;\n"
+      "L31: mov.b32 %0, %65; mov.b32 %1, %66; bra.uni LEND;\n"
+      "LEND:\n}"
+      : "=f"(vx), "=f"(vy)
+      : "r"(i & 31),
+        "f"(R[0].x), "f"(R[0].y), "f"(R[1].x), "f"(R[1].y), "f"(R[2].x), "f"(R[2].y), "f"(R[3].x), "f"(R[3].y),
+        "f"(R[4].x), "f"(R[4].y), "f"(R[5].x), "f"(R[5].y), "f"(R[6].x), "f"(R[6].y), "f"(R[7].x), "f"(R[7].y),
+        "f"(R[8].x), "f"(R[8].y), "f"(R[9].x), "f"(R[9].y), "f"(R[10].x), "f"(R[10].y), "f"(R[11].x), "f"(R[11].y),
+        "f"(R[12].x), "f"(R[12].y), "f"(R[13].x), "f"(R[13].y), "f"(R[14].x), "f"(R[14].y), "f"(R[15].x), "f"(R[15].y),
+        "f"(R[16].x), "f"(R[16].y), "f"(R[17].x), "f"(R[17].y), "f"(R[18].x), "f"(R[18].y), "f"(R[19].x), "f"(R[19].y),
+        "f"(R[20].x), "f"(R[20].y), "f"(R[21].x), "f"(R[21].y), "f"(R[22].x), "f"(R[22].y), "f"(R[23].x), "f"(R[23].y),
+        "f"(R[24].x), "f"(R[24].y), "f"(R[25].x), "f"(R[25].y), "f"(R[26].x), "f"(R[26].y), "f"(R[27].x), "f"(R[27].y),
+        "f"(R[28].x), "f"(R[28].y), "f"(R[29].x), "f"(R[29].y), "f"(R[30].x), "f"(R[30].y), "f"(R[31].x), "f"(R[31].y));
+  return make_float2(vx, vy);
+}
+
+__device__ __forceinline__ float2 select_reg16(const float2 (&R)[16], int i) {
+  float vx, vy;
+  asm volatile(
+      "{\n"
+      "ts: .branchtargets L0, L1, L2, L3, L4, L5, L6, L7, L8, L9, L10, L11, L12, L13, L14, L15;\n"
+      "brx.idx.uni %2, ts;\n"
+      "L0: mov.b32 %0, %3; mov.b32 %1, %4; bra.uni LEND;\n"
+      "L1: mov.b32 %0, %5; mov.b32 %1, %6; bra.uni LEND;\n"
+      "L2: mov.b32 %0, %7; mov.b32 %1, %8; bra.uni LEND;\n"
+      "L3: mov.b32 %0, %9; mov.b32 %1, %10; bra.uni LEND;\n"
+      "L4: mov.b32 %0, %11; mov.b32 %1, %12; bra.uni LEND;\n"
+      "L5: mov.b32 %0, %13; mov.b32 %1, %14; bra.uni LEND;\n"
+      "L6: mov.b32 %0, %15; mov.b32 %1, %16; bra.uni LEND;\n"
+      "L7: mov.b32 %0, %17; mov.b32 %1, %18; bra.uni LEND;\n"
+      "L8: mov.b32 %0, %19; mov.b32 %1, %20; bra.uni LEND;\n"
+      "L9: mov.b32 %0, %21; mov.b32 %1, %22; bra.uni LEND;\n"
+      "L10: mov.b32 %0, %23; mov.b32 %1, %24; bra.uni LEND;\n"
+      "L11: mov.b32 %0, %25; mov.b32 %1, %26; bra.uni LEND;\n"
+      "L12: mov.b32 %0, %27; mov.b32 %1, %28; bra.uni LEND;\n"
+      "L13: mov.b32 %0, %29; mov.b32 %1, %30; bra.uni LEND;\n"
+      "L14: mov.b32 %0, %31; mov.b32 %1, %32; bra.uni LEND;\n"
+      "L15: mov.b32 %0, %33; mov.b32 %1, %34; bra.uni LEND;\n"
+      "LEND:\n}"
+      : "=f"(vx), "=f"(vy)
+      : "r"(i & 15),
+        "f"(R[0].x), "f"(R[0].y), "f"(R[1].x), "f"(R[1].y), "f"(R[2].x), "f"(R[2].y), "f"(R[3].x), "f"(R[3].y),
+        "f"(R[4].x), "f"(R[4].y), "f"(R[5].x), "f"(R[5].y), "f"(R[6].x), "f"(R[6].y), "f"(R[7].x), "f"(R[7].y),
+        "f"(R[8].x), "f"(R[8].y), "f"(R[9].x), "f"(R[9].y), "f"(R[10].x), "f"(R[10].y), "f"(R[11].x), "f"(R[11].y),
+        "f"(R[12].x), "f"(R[12].y), "f"(R[13].x), "f"(R[13].y), "f"(R[14].x), "f"(R[14].y), "f"(R[15].x), "f"(R[15].y));
+  return make_float2(vx, vy);
+}
+
 template <int N>
 __device__ __forceinline__ float2 select_reg(const float2 (&R)[N], int i) {
-  float2 v;
   if constexpr (N == 64) {
-    if (i < 32) {
-      const float2(&lo)[32] = *reinterpret_cast<const float2(*)[32]>(&R[0]);
-      FSE_SEL32(lo, i, v);
-    } else {
-      const float2(&hi)[32] = *reinterpret_cast<const float2(*)[32]>(&R[32]);
-      FSE_SEL32(hi, i - 32, v);
-    }
+    const float2(&lo)[32] = *reinterpret_cast<const float2(*)[32]>(&R[0]);
+    const float2(&hi)[32] = *reinterpret_cast<const float2(*)[32]>(&R[32]);
+    return i < 32 ? select_reg32(lo, i) : select_reg32(hi, i - 32);
   } else if constexpr (N == 32) {
-    FSE_SEL32(R, i, v);
+    return select_reg32(R, i);
   } else {
-    switch (i) {
-      case 0: v = R[0]; break;   case 1: v = R[1]; break;
-      case 2: v = R[2]; break;   case 3: v = R[3]; break;
-      case 4: v = R[4]; break;   case 5: v = R[5]; break;
-      case 6: v = R[6]; break;   case 7: v = R[7]; break;
-      case 8: v = R[8]; break;   case 9: v = R[9]; break;
-      case 10: v = R[10]; break; case 11: v = R[11]; break;
-      case 12: v = R[12]; break; case 13: v = R[13]; break;
-      case 14: v = R[14]; break; default: v = R[15]; break;
-    }
+    return select_reg16(R, i);
   }
-  return v;
 }
 
 // An opaque register copy of a constant, so that "(bits & m) | imm" stays a
