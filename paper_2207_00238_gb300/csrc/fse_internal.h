@@ -48,18 +48,23 @@ struct TileDev {
   int64_t val_off;  // first pixel of this tile's value plane (elements)
 };
 
-// Per-class work queue: items become ready when every block they depend on
-// is done; consumers pop slots in order and wait (bounded) for the slot's
-// producer.
+// Per-class ready queue with priority levels: an item is pushed into the
+// queue of its level (its PHASED phase, capped) once every block it depends on
+// is done; consumers claim an already-pushed item from the lowest non-empty
+// level.  Level l owns slots [sum of lcnt below l, + lcnt[l]).
+constexpr int NLEV = 32;
 struct QueueDev {
   int32_t n_items;  // items of this class (written by the planner)
-  int32_t head;     // next slot to pop
-  int32_t tail;     // next slot to push
-  int32_t n_done;
+  int32_t claimed;  // items handed to consumers
+  int32_t n_done;   // items finished (progress watchdog of waiting consumers)
   int32_t n_empty;
   int32_t n_core;   // lost blocks that touch their tile's core
   int32_t error;    // ErrBits
   int32_t error_info;
+  int32_t pad;
+  int32_t lcnt[NLEV];   // items per level
+  int32_t lhead[NLEV];  // claimed per level
+  int32_t ltail[NLEV];  // pushed per level
 };
 
 struct ClassArgs {

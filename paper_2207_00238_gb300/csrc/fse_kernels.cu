@@ -66,30 +66,89 @@ __device__ __forceinline__ int64_t order_key(const JobDev& J, int I, int Jb) {
   return k;
 }
 
-// Pops the next ready item: >= 0 item id, -1 queue drained, -2 error.
-__device__ __forceinline__ int queue_pop(const ClassArgs& C, int64_t timeout_ns) {
-  const int n = min(ld_relaxed(&C.q->n_items), C.cap);
-  const int pos = atomicAdd(&C.q->head, 1);
-  if (pos >= n) return -1;
-  const uint64_t t0 = global_ns();
-  unsigned sleep_ns = 32;
-  int v;
-  while ((v = ld_acquire(&C.slots[pos])) < 0) {
-    if (ld_relaxed(&C.q->error) != 0) return -2;
-    if ((int64_t)(global_ns() - t0) > timeout_ns) {
-      atomicOr(&C.q->error, ERR_TIMEOUT);
-      C.q->error_info = pos;
+// Priority level of an item: its PHASED phase (capped), 0 for other orders.
+__device__ __forceinline__ int item_level(const JobDev& J, int I, int Jb) {
+  if (J.order != ORDER_PHASED) return 0;
+  return min((I % J.P) * J.P + (Jb % J.P), NLEV - 1);
+}
+
+// First slot of level l: levels are laid out one after another.
+__device__ __forceinline__ int level_offset(const QueueDev* q, int l) {
+  int o = 0;
+  for (int k = 0; k < l; ++k) o += __ldcg(&q->lcnt[k]);
+  return o;
+}
+
+__device__ __forceinline__ void queue_push(const ClassArgs& C, int item, int lvl) {
+  const int pos = atomicAdd(&C.q->ltail[lvl], 1);
+  st_release(&C.slots[level_offset(C.q, lvl) + pos], item);
+}
+
+// Warp-cooperative pop (all 32 lanes call it): claims a pushed item from the
+// lowest non-empty level.  Returns the item id, -1 once every item has been
+// claimed, -2 on error.  A waiting warp gives up with ERR_TIMEOUT when no item
+// of the class finished for timeout_ns (progress watchdog, wall clock).
+__device__ int queue_pop_warp(const ClassArgs& C, int64_t timeout_ns, int lane) {
+  QueueDev* q = C.q;
+  const int n = __shfl_sync(0xffffffffu, min(ld_relaxed(&q->n_items), C.cap), 0);
+  int last_done = -1;
+  unsigned long long t_last = 0;
+  unsigned sleep_ns = 64;
+  for (;;) {
+    const int h = ld_relaxed(&q->lhead[lane]);
+    const int tl = ld_relaxed(&q->ltail[lane]);
+    const unsigned avail = __ballot_sync(0xffffffffu, h < tl);
+    if (avail) {
+      const int l = __ffs(avail) - 1;
+      int pos = -1;
+      if (lane == l && atomicCAS(&q->lhead[l], h, h + 1) == h) pos = h;
+      pos = __shfl_sync(0xffffffffu, pos, l);
+      if (pos < 0) continue;  // another consumer won this slot: rescan
+      int item = 0;
+      if (lane == 0) {
+        // the producer bumped ltail just before writing the slot
+        int* slot = &C.slots[level_offset(q, l) + pos];
+        const uint64_t t0 = global_ns();
+        while ((item = ld_acquire(slot)) < 0) {
+          if ((int64_t)(global_ns() - t0) > timeout_ns) {
+            atomicOr(&q->error, ERR_TIMEOUT);
+            q->error_info = pos;
+            item = -2;
+            break;
+          }
+        }
+        if (item >= 0) atomicAdd(&q->claimed, 1);
+      }
+      return __shfl_sync(0xffffffffu, item, 0);
+    }
+    // every exit decision is taken on lane 0's reads, broadcast to the warp
+    int claimed = 0, err = 0, done = 0;
+    unsigned long long now = 0;
+    if (lane == 0) {
+      claimed = ld_relaxed(&q->claimed);
+      err = ld_relaxed(&q->error);
+      done = ld_relaxed(&q->n_done);
+      now = global_ns();
+    }
+    claimed = __shfl_sync(0xffffffffu, claimed, 0);
+    err = __shfl_sync(0xffffffffu, err, 0);
+    done = __shfl_sync(0xffffffffu, done, 0);
+    now = __shfl_sync(0xffffffffu, now, 0);
+    if (claimed >= n) return -1;
+    if (err != 0) return -2;
+    if (done != last_done) {
+      last_done = done;
+      t_last = now;
+    } else if ((int64_t)(now - t_last) > timeout_ns) {
+      if (lane == 0) {
+        atomicOr(&q->error, ERR_TIMEOUT);
+        q->error_info = -1;
+      }
       return -2;
     }
     __nanosleep(sleep_ns);
-    if (sleep_ns < 2048) sleep_ns <<= 1;
+    if (sleep_ns < 1024) sleep_ns <<= 1;
   }
-  return v;
-}
-
-__device__ __forceinline__ void queue_push(const ClassArgs& C, int item) {
-  const int pos = atomicAdd(&C.q->tail, 1);
-  st_release(&C.slots[pos], item);
 }
 
 // After a block's writes are globally visible: decrement the pending count
@@ -107,7 +166,7 @@ __device__ __forceinline__ void release_successors(const ExecArgs& a, const Clas
     if (id2 < 0 || order_key(J, I2, J2) <= kx) continue;
     if (atomicSub(&C.cnt[id2], 1) == 1) {
       __threadfence();
-      queue_push(C, id2);
+      queue_push(C, id2, item_level(J, I2, J2));
     }
   }
 }
@@ -579,9 +638,7 @@ __global__ void __launch_bounds__(NW32 * 32, 5) k_exec_f32_32(const __grid_const
     return;
   }
   for (;;) {
-    int id = 0;
-    if (lane == 0) id = queue_pop(C, a.timeout_ns);
-    id = __shfl_sync(0xffffffffu, id, 0);
+    const int id = queue_pop_warp(C, a.timeout_ns, lane);
     if (id < 0) break;
     item_f32_32(a, id, sm, tw, lane);
     __threadfence();
@@ -778,7 +835,10 @@ __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : 3)) k
     return;
   }
   for (;;) {
-    if (t == 0) sm.item = queue_pop(C, a.timeout_ns);
+    if (t < 32) {
+      const int id = queue_pop_warp(C, a.timeout_ns, t);
+      if (t == 0) sm.item = id;
+    }
     __syncthreads();
     const int id = sm.item;
     if (id < 0) break;
@@ -958,7 +1018,10 @@ __global__ void __launch_bounds__(NT64) k_exec_f64(const __grid_constant__ ExecA
     return;
   }
   for (;;) {
-    if (t == 0) sm.item = queue_pop(C, a.timeout_ns);
+    if (t < 32) {
+      const int id = queue_pop_warp(C, a.timeout_ns, t);
+      if (t == 0) sm.item = id;
+    }
     __syncthreads();
     const int id = sm.item;
     if (id < 0) break;
@@ -1017,6 +1080,7 @@ __global__ void k_mark(const __grid_constant__ ExecArgs a) {
       id = atomicAdd(&C.q->n_items, 1);
       if (id < C.cap) {
         C.items[id] = make_int2(blockIdx.y, (I << 16) | Jb);
+        atomicAdd(&C.q->lcnt[item_level(J, I, Jb)], 1);
         if (core) atomicAdd(&C.q->n_core, 1);
       } else {
         atomicOr(&C.q->error, ERR_BOUNDS);
@@ -1052,13 +1116,13 @@ __global__ void k_deps(const __grid_constant__ ExecArgs a, int cls) {
     C.cnt[id] = cnt;
     if (a.level_of) a.level_of[(size_t)cls * a.level_stride + id] =
         J.order == ORDER_PHASED ? (I % J.P) * J.P + (Jb % J.P) : 0;
-    if (cnt == 0) queue_push(C, id);
+    if (cnt == 0) queue_push(C, id, item_level(J, I, Jb));
   }
 }
 
 __global__ void k_probe(const __grid_constant__ ExecArgs a) {
-  const int id = queue_pop(a.c[0], a.timeout_ns);
-  if (id >= 0) atomicAdd(&a.c[0].q->n_done, 1);
+  const int id = queue_pop_warp(a.c[0], a.timeout_ns, threadIdx.x & 31);
+  if (id >= 0 && threadIdx.x == 0) atomicAdd(&a.c[0].q->n_done, 1);
 }
 
 // ===========================================================================
@@ -1134,7 +1198,7 @@ cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st) {
 }
 
 cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st) {
-  k_probe<<<1, 1, 0, st>>>(a);
+  k_probe<<<1, 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
