@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "fse_internal.h"
 
@@ -334,19 +335,29 @@ __device__ __forceinline__ void eval_and_write(const TileDev& T, const JobDev& J
                                const int* coef_u, const real2* coef_d, const real2* tw,
                                real* red, int t, int nthr) {
   const int b = J.b, np = b * b, K = J.K, F = J.F, B = J.B;
-  const int tstep = 64 / F;
+  const int logF = F == 32 ? 5 : 6, tshift = 6 - logF;  // tw has 64 entries
   const int nsplit = np <= nthr ? nthr / np : 1;
   for (int p0 = 0; p0 < np; p0 += nthr / nsplit) {
     const int p = p0 + t % (nthr / nsplit), s = t / (nthr / nsplit);
-    real g = 0;
+    real g = 0, g2 = 0;
     if (p < np && s < nsplit) {
       const int m = B + p / b, n = B + p % b;
-      for (int nu = s; nu < K; nu += nsplit) {
+      int nu = s;
+      for (; nu + nsplit < K; nu += 2 * nsplit) {  // two independent chains
+        const int ua = coef_u[nu], ub = coef_u[nu + nsplit];
+        const int qa = ((((ua >> logF) * m + (ua & (F - 1)) * n) & (F - 1)) << tshift);
+        const int qb = ((((ub >> logF) * m + (ub & (F - 1)) * n) & (F - 1)) << tshift);
+        const real2 da = coef_d[nu], ea = tw[qa], db = coef_d[nu + nsplit], eb = tw[qb];
+        g += da.x * ea.x - da.y * ea.y;
+        g2 += db.x * eb.x - db.y * eb.y;
+      }
+      for (; nu < K; nu += nsplit) {
         const int u = coef_u[nu];
-        const int q = (((u / F) * m + (u % F) * n) & (F - 1)) * tstep;
+        const int q = ((((u >> logF) * m + (u & (F - 1)) * n) & (F - 1)) << tshift);
         const real2 d = coef_d[nu], e = tw[q];
         g += d.x * e.x - d.y * e.y;
       }
+      g += g2;
     }
     red[t] = g;
     bar<CTA>();
@@ -486,12 +497,34 @@ __device__ __forceinline__ float2 select_reg(const float2 (&R)[N], int i) {
   }
 }
 
-// An opaque register copy of a constant, so that "(bits & m) | imm" stays a
-// single three-input logic op instead of two immediate ones.
+// An opaque register copy of a constant.
 __device__ __forceinline__ uint32_t opaque(uint32_t v) {
   uint32_t r;
   asm volatile("mov.b32 %0, %1;" : "=r"(r) : "r"(v));
   return r;
+}
+
+// Argmax key of one bin: (energy bits & mask) | index bits, as one three-input
+// logic op (LUT 0xEA = (a & b) | c).
+template <uint32_t IDX>
+__device__ __forceinline__ uint32_t make_key(float e, uint32_t mask) {
+  uint32_t k;
+  asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(k) : "r"(__float_as_uint(e)), "r"(mask), "n"(IDX));
+  return k;
+}
+
+// Three-input unsigned max.
+__device__ __forceinline__ uint32_t max3u(uint32_t a, uint32_t b, uint32_t c) {
+  return max(a, max(b, c));
+}
+
+// Static loop helper: f(std::integral_constant<int, I>) for I = 0..N-1.
+template <int I, int N, typename Fn>
+__device__ __forceinline__ void static_for(Fn&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
 }
 
 // ===========================================================================
@@ -577,13 +610,15 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
   float2(&R)[32] = x;
 
   const uint32_t kmask = opaque(0xFFFFFC00u);
-  uint32_t bq[4] = {0u, 0u, 0u, 0u};  // four independent max chains
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const float e = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
-    bq[j & 3] = max(bq[j & 3], (__float_as_uint(e) & kmask) | (uint32_t)((31 - j) << 5));
-  }
-  uint32_t best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | (uint32_t)(31 - lane);
+  uint32_t bq[2] = {0u, 0u};  // two independent max chains, three-input max
+  static_for<0, 16>([&](auto h) {
+    constexpr int j = 2 * decltype(h)::value;
+    const float e0 = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
+    const float e1 = fmaf(R[j + 1].y, R[j + 1].y, R[j + 1].x * R[j + 1].x);
+    bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<(31u - j) << 5>(e0, kmask),
+                             make_key<(30u - j) << 5>(e1, kmask));
+  });
+  uint32_t best = max(bq[0], bq[1]) | (uint32_t)(31 - lane);
   for (int iter = 0; iter < K; ++iter) {
     best = __reduce_max_sync(0xffffffffu, best);
     const int flat = 1023 - (int)(best & 1023u);
@@ -595,25 +630,32 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
     if (lane == 0) {
       sm.coef_u[iter] = flat;
       sm.coef_d[iter] = make_float2(dx, dy);
-      debug_useq(a, CLS_F32_32, id, iter, flat);
     }
     if (iter + 1 == K) break;
     const float2* wp = sm.Wd + (32 - u1) * 32 + ((lane - u2) & 31);
-    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
+    const float ndx = -dx, ndy = -dy;
+    bq[0] = bq[1] = 0u;
+    static_for<0, 16>([&](auto h) {
+      constexpr int j = 2 * decltype(h)::value;
+      float e[2];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float2 w = wp[j * 32];
-      float rx = fmaf(-dx, w.x, R[j].x);
-      rx = fmaf(dy, w.y, rx);
-      float ry = fmaf(-dx, w.y, R[j].y);
-      ry = fmaf(-dy, w.x, ry);
-      R[j] = make_float2(rx, ry);
-      const float e = fmaf(ry, ry, rx * rx);
-      bq[j & 3] = max(bq[j & 3], (__float_as_uint(e) & kmask) | (uint32_t)((31 - j) << 5));
-    }
-    best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | (uint32_t)(31 - lane);
+      for (int k = 0; k < 2; ++k) {
+        const float2 w = wp[(j + k) * 32];
+        float rx = fmaf(ndx, w.x, R[j + k].x);
+        rx = fmaf(dy, w.y, rx);
+        float ry = fmaf(ndx, w.y, R[j + k].y);
+        ry = fmaf(ndy, w.x, ry);
+        R[j + k] = make_float2(rx, ry);
+        e[k] = fmaf(ry, ry, rx * rx);
+      }
+      bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<(31u - j) << 5>(e[0], kmask),
+                               make_key<(30u - j) << 5>(e[1], kmask));
+    });
+    best = max(bq[0], bq[1]) | (uint32_t)(31 - lane);
   }
   __syncwarp();
+  if (a.dbg_useq)
+    for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
   eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
                                        32);
 }
@@ -756,13 +798,15 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   const uint32_t kmask = opaque(0xFFFFF000u);
   const uint32_t tbits = (uint32_t)(((NQ - 1 - q) * RPT) << 6) | (uint32_t)(63 - c);
 
-  uint32_t bq[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-  for (int i = 0; i < RPT; ++i) {
-    const float e = fmaf(R[i].y, R[i].y, R[i].x * R[i].x);
-    bq[i & 3] = max(bq[i & 3], (__float_as_uint(e) & kmask) | (uint32_t)((RPT - 1 - i) << 6));
-  }
-  uint32_t best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | tbits;
+  uint32_t bq[2] = {0u, 0u};
+  static_for<0, RPT / 2>([&](auto h) {
+    constexpr int i = 2 * decltype(h)::value;
+    const float e0 = fmaf(R[i].y, R[i].y, R[i].x * R[i].x);
+    const float e1 = fmaf(R[i + 1].y, R[i + 1].y, R[i + 1].x * R[i + 1].x);
+    bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i) << 6>(e0, kmask),
+                             make_key<(uint32_t)(RPT - 2 - i) << 6>(e1, kmask));
+  });
+  uint32_t best = max(bq[0], bq[1]) | tbits;
   for (int iter = 0; iter < K; ++iter) {
     best = __reduce_max_sync(0xffffffffu, best);
     {
@@ -789,25 +833,32 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     if (t == 0) {
       sm.coef_u[iter] = flat;
       sm.coef_d[iter] = make_float2(dx, dy);
-      debug_useq(a, CLS_F32_64, id, iter, flat);
     }
     if (iter + 1 == K) break;
     const float2* wp = sm.Wd + (RPT * q - u1 + 64) * 64 + ((c - u2) & 63);
-    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
+    const float ndx = -dx, ndy = -dy;
+    bq[0] = bq[1] = 0u;
+    static_for<0, RPT / 2>([&](auto h) {
+      constexpr int i = 2 * decltype(h)::value;
+      float e[2];
 #pragma unroll
-    for (int i = 0; i < RPT; ++i) {
-      const float2 w = wp[i * 64];
-      float rx = fmaf(-dx, w.x, R[i].x);
-      rx = fmaf(dy, w.y, rx);
-      float ry = fmaf(-dx, w.y, R[i].y);
-      ry = fmaf(-dy, w.x, ry);
-      R[i] = make_float2(rx, ry);
-      const float e = fmaf(ry, ry, rx * rx);
-      bq[i & 3] = max(bq[i & 3], (__float_as_uint(e) & kmask) | (uint32_t)((RPT - 1 - i) << 6));
-    }
-    best = max(max(bq[0], bq[1]), max(bq[2], bq[3])) | tbits;
+      for (int k = 0; k < 2; ++k) {
+        const float2 w = wp[(i + k) * 64];
+        float rx = fmaf(ndx, w.x, R[i + k].x);
+        rx = fmaf(dy, w.y, rx);
+        float ry = fmaf(ndx, w.y, R[i + k].y);
+        ry = fmaf(ndy, w.x, ry);
+        R[i + k] = make_float2(rx, ry);
+        e[k] = fmaf(ry, ry, rx * rx);
+      }
+      bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i) << 6>(e[0], kmask),
+                               make_key<(uint32_t)(RPT - 2 - i) << 6>(e[1], kmask));
+    });
+    best = max(bq[0], bq[1]) | tbits;
   }
   __syncthreads();
+  if (a.dbg_useq)
+    for (int k = t; k < K; k += NT) debug_useq(a, CLS_F32_64, id, k, sm.coef_u[k]);
   eval_and_write<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
                                       NT);
 }
