@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--arena-mb", type=int, default=4096)
-    ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 8])
+    ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 8])
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     return ap.parse_args()
 

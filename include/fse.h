@@ -140,9 +140,10 @@ void fse_context_destroy(fse_context_t* ctx);
 #define FSE_OPT_USE_GRAPH 4     /* 1 = capture each batch in a CUDA graph and
                                    replay it while the job set is unchanged    */
 #define FSE_OPT_DEBUG_CAPTURE 5 /* 1 = record each block's selected bins       */
-#define FSE_OPT_F64_WARPS 7     /* warps per block of the F = 64 FP32 executor:
-                                   2 (64 bins per thread), 4 (32) or 8 (16);
-                                   0 = default                                */
+#define FSE_OPT_F64_WARPS 7     /* layout of the F = 64 FP32 executor: warps per
+                                   block 2 (64 bins per thread), 4 (32) or 8 (16);
+                                   5 = 4 warps with a 96-row W table (4 blocks
+                                   per SM); 0 = default                        */
 #define FSE_OPT_KERNEL_TIMING 6 /* 1 = bracket the iteration kernels of every
                                    call with CUDA events (no synchronisation);
                                    read with fse_context_kernel_times         */

@@ -73,7 +73,8 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       c->debug = value != 0;
       return FSE_OK;
     case FSE_OPT_F64_WARPS: {
-      if (value != 0 && value != 2 && value != 4 && value != 8) return fse::fail(FSE_EINVAL, "f64 warps");
+      if (value != 0 && value != 2 && value != 4 && value != 5 && value != 8)
+        return fse::fail(FSE_EINVAL, "f64 warps");
       fse::set_f64_warps(value == 0 ? 4 : (int)value);
       int nb = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fse::exec_kernel_ptr(fse::CLS_F32_64),

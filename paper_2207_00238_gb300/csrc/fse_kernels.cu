@@ -505,11 +505,11 @@ __device__ __forceinline__ uint32_t opaque(uint32_t v) {
 }
 
 // Argmax key of one bin: (energy bits & mask) | index bits, as one three-input
-// logic op (LUT 0xEA = (a & b) | c).
+// logic op with the index as the immediate operand (LUT 0xEC = (a & c) | b).
 template <uint32_t IDX>
 __device__ __forceinline__ uint32_t make_key(float e, uint32_t mask) {
   uint32_t k;
-  asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(k) : "r"(__float_as_uint(e)), "r"(mask), "n"(IDX));
+  asm("lop3.b32 %0, %1, %2, %3, 0xEC;" : "=r"(k) : "r"(__float_as_uint(e)), "n"(IDX), "r"(mask));
   return k;
 }
 
@@ -699,9 +699,10 @@ __global__ void __launch_bounds__(NW32 * 32, 5) k_exec_f32_32(const __grid_const
 // (redux), then an NWB-way exchange through shared memory behind one
 // barrier, double-buffered by iteration parity.
 // ===========================================================================
-template <int NWB>
+template <int NWB, int ROWS = 128>
 struct alignas(16) CtaSmem64 {
-  float2 Wd[128 * 64];   // rows 0..127: W rows (r mod 64); 64..127 double as FFT buffer
+  float2 Wd[ROWS * 64];  // W rows (r mod 64); ROWS = 128: 64..127 double as FFT buffer,
+                         // ROWS = 96: 0..63 are the FFT buffer, 64..95 copy rows 0..31
   float2 coef_d[KMAX];
   int32_t coef_u[KMAX];
   float2 tw[64];
@@ -712,8 +713,8 @@ struct alignas(16) CtaSmem64 {
   JobDev J;
 };
 
-template <int NWB>
-__device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64<NWB>& sm, int t) {
+template <int NWB, int ROWS>
+__device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
   constexpr int NT = NWB * 32, RPT = 4096 / NT, NQ = NT / 64;
   const ClassArgs& C = a.c[CLS_F32_64];
   const int2 it = C.items[id];
@@ -727,7 +728,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   const int S = J.S, K = J.K;
   float* val = a.val_f + T.val_off;
   if (t == 0) debug_record(a, CLS_F32_64, id, T, it.x, I, Jb);
-  float2* zbuf = sm.Wd + 64 * 64;
+  float2* zbuf = ROWS == 128 ? sm.Wd + 64 * 64 : sm.Wd;
 
   stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, NT);
   __syncthreads();
@@ -771,7 +772,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   __syncthreads();
   const int c = t & 63, q = t >> 6, lane = t & 31, warp = t >> 5;
   float2 R[RPT];
-  {
+  if constexpr (ROWS == 128) {
     const int cm = (64 - c) & 63;
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
@@ -780,14 +781,49 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       sm.Wd[k1 * 64 + c] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
       R[i] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
     }
-  }
-  __syncthreads();
+    __syncthreads();
 #pragma unroll
-  for (int i = 0; i < RPT; ++i) {
-    const int k1 = i + RPT * q;
-    sm.Wd[(k1 + 64) * 64 + c] = sm.Wd[k1 * 64 + c];
+    for (int i = 0; i < RPT; ++i) {
+      const int k1 = i + RPT * q;
+      sm.Wd[(k1 + 64) * 64 + c] = sm.Wd[k1 * 64 + c];
+    }
+    __syncthreads();
+  } else {
+    // R = (Z(k) - conj Z(-k)) / 2i into registers (reads only)
+    const int cm = (64 - c) & 63;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int k1 = i + RPT * q, k1m = (64 - k1) & 63;
+      const float2 z = zbuf[swz<64>(k1, c)], zm = zbuf[swz<64>(k1m, cm)];
+      R[i] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    }
+    __syncthreads();
+    // W = (Z(k) + conj Z(-k)) / 2 in place, unswizzled.  The swizzle permutes
+    // within a row, so a warp that owns rows k1 and -k1 touches no other
+    // warp's data; all its reads precede its writes.
+    for (int rp = warp; rp <= 32; rp += NWB) {
+      const int k1 = rp, k1m = (64 - rp) & 63;
+      float2 wa[2], wb[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cc = lane + 32 * h, ccm = (64 - cc) & 63;
+        const float2 z = zbuf[swz<64>(k1, cc)], zm = zbuf[swz<64>(k1m, ccm)];
+        wa[h] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));  // W(k1, cc)
+        wb[h] = make_float2(wa[h].x, -wa[h].y);                        // W(-k1, -cc)
+      }
+      __syncwarp();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cc = lane + 32 * h, ccm = (64 - cc) & 63;
+        sm.Wd[k1 * 64 + cc] = wa[h];
+        sm.Wd[k1m * 64 + ccm] = wb[h];
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int e = t; e < 32 * 64; e += NT) sm.Wd[64 * 64 + e] = sm.Wd[e];
+    __syncthreads();
   }
-  __syncthreads();
   const float W0 = sm.Wd[0].x;
   if (!(W0 > 0.f)) {
     if (t == 0) atomicAdd(&C.q->n_empty, 1);
@@ -835,7 +871,9 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       sm.coef_d[iter] = make_float2(dx, dy);
     }
     if (iter + 1 == K) break;
-    const float2* wp = sm.Wd + (RPT * q - u1 + 64) * 64 + ((c - u2) & 63);
+    const int r0 = RPT * q - u1;  // first W row of this thread, mod 64
+    const float2* wp =
+        sm.Wd + (ROWS == 128 ? r0 + 64 : (r0 < 0 ? r0 + 64 : r0)) * 64 + ((c - u2) & 63);
     const float ndx = -dx, ndy = -dy;
     bq[0] = bq[1] = 0u;
     static_for<0, RPT / 2>([&](auto h) {
@@ -863,24 +901,25 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
                                       NT);
 }
 
-template <int NWB>
-__global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : 3)) k_exec_f32_64(const __grid_constant__ ExecArgs a) {
+template <int NWB, int ROWS = 128>
+__global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS == 96 ? 4 : 3)))
+    k_exec_f32_64(const __grid_constant__ ExecArgs a) {
   constexpr int NT = NWB * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CtaSmem64<NWB>& sm = *reinterpret_cast<CtaSmem64<NWB>*>(smem_raw);
+  CtaSmem64<NWB, ROWS>& sm = *reinterpret_cast<CtaSmem64<NWB, ROWS>*>(smem_raw);
   const int t = threadIdx.x;
   if (t < 64) sm.tw[t] = make_float2(c_twf[t].x, -c_twf[t].y);
   __syncthreads();
   const ClassArgs& C = a.c[CLS_F32_64];
   if (a.single_item >= 0) {
-    if (blockIdx.x == 0) item_f32_64<NWB>(a, a.single_item, sm, t);
+    if (blockIdx.x == 0) item_f32_64<NWB, ROWS>(a, a.single_item, sm, t);
     return;
   }
   if (a.level_mode) {
     const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x; id < n; id += gridDim.x)
       if (a.level_of[(size_t)CLS_F32_64 * a.level_stride + id] == a.level) {
-        item_f32_64<NWB>(a, id, sm, t);
+        item_f32_64<NWB, ROWS>(a, id, sm, t);
         __syncthreads();
       }
     return;
@@ -893,7 +932,7 @@ __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : 3)) k
     __syncthreads();
     const int id = sm.item;
     if (id < 0) break;
-    item_f32_64<NWB>(a, id, sm, t);
+    item_f32_64<NWB, ROWS>(a, id, sm, t);
     __threadfence();
     __syncthreads();
     const int2 it = C.items[id];
@@ -1180,22 +1219,26 @@ __global__ void k_probe(const __grid_constant__ ExecArgs a) {
 // launchers
 // ===========================================================================
 int g_nwb64 = 4;  // warps per block of the F = 64 executor (4 or 8)
-void set_f64_warps(int nwb) { g_nwb64 = (nwb == 8 || nwb == 2) ? nwb : 4; }
+void set_f64_warps(int nwb) { g_nwb64 = (nwb == 8 || nwb == 2 || nwb == 5) ? nwb : 4; }
 int get_f64_warps() { return g_nwb64; }
 int exec_threads(int cls) {
-  return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? g_nwb64 * 32 : NT64);
+  return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? (g_nwb64 == 5 ? 4 : g_nwb64) * 32 : NT64);
 }
 size_t exec_smem(int cls) {
   if (cls == CLS_F32_32) return SMEM32;
   if (cls == CLS_F32_64)
-    return g_nwb64 == 8 ? sizeof(CtaSmem64<8>) : (g_nwb64 == 2 ? sizeof(CtaSmem64<2>) : sizeof(CtaSmem64<4>));
+    return g_nwb64 == 8 ? sizeof(CtaSmem64<8>)
+                        : (g_nwb64 == 2 ? sizeof(CtaSmem64<2>)
+                                        : (g_nwb64 == 5 ? sizeof(CtaSmem64<4, 96>) : sizeof(CtaSmem64<4>)));
   return SMEMD;
 }
 const void* exec_kernel_ptr(int cls) {
   if (cls == CLS_F32_32) return (const void*)k_exec_f32_32;
   if (cls == CLS_F32_64)
     return g_nwb64 == 8 ? (const void*)k_exec_f32_64<8>
-                        : (g_nwb64 == 2 ? (const void*)k_exec_f32_64<2> : (const void*)k_exec_f32_64<4>);
+                        : (g_nwb64 == 2 ? (const void*)k_exec_f32_64<2>
+                                        : (g_nwb64 == 5 ? (const void*)k_exec_f32_64<4, 96>
+                                                        : (const void*)k_exec_f32_64<4>));
   return (const void*)k_exec_f64;
 }
 
@@ -1211,6 +1254,9 @@ cudaError_t exec_setup(int device) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_exec_f32_64<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(CtaSmem64<2>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_exec_f32_64<4, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(CtaSmem64<4, 96>));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_exec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEMD);
 }
@@ -1242,6 +1288,8 @@ cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st) {
     k_exec_f32_64<8><<<grid, 256, sizeof(CtaSmem64<8>), st>>>(a);
   else if (cls == CLS_F32_64 && g_nwb64 == 2)
     k_exec_f32_64<2><<<grid, 64, sizeof(CtaSmem64<2>), st>>>(a);
+  else if (cls == CLS_F32_64 && g_nwb64 == 5)
+    k_exec_f32_64<4, 96><<<grid, 128, sizeof(CtaSmem64<4, 96>), st>>>(a);
   else if (cls == CLS_F32_64)
     k_exec_f32_64<4><<<grid, 128, sizeof(CtaSmem64<4>), st>>>(a);
   else k_exec_f64<<<grid, NT64, SMEMD, st>>>(a);
