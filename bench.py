@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--arena-mb", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="measured requests of the serving leg (0 = skip)")
     ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 8])
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     return ap.parse_args()
@@ -171,6 +173,68 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# serving leg: Poisson arrivals into the continuous-batching server
+# ---------------------------------------------------------------------------
+def serve_leg(fse, device, n_measured, n_warm=100, pool_size=16, rate_hz=200.0):
+    """Requests follow the serving workload: Poisson arrivals (mean 200/s),
+    areas log-uniform in 128^2 .. 7680x4320, 1-30 % of the 8x8 blocks lost,
+    K in 100..200.  Images come from a pool of pool_size seeded requests,
+    reused cyclically; arrival times are drawn for every request."""
+    import threading
+    from paper_2207_00238_gb300 import synth
+    stream = synth.serving_stream(n_requests=pool_size)
+    pool = [job for _, job in stream]
+    rng = synth.Rng(synth.SEED_BASE + 55)
+    n = n_warm + n_measured
+    gaps = -np.log1p(-rng.uniform(n)) / rate_hz
+    arrivals = np.cumsum(gaps)
+    ctx = fse.Context(device, arena_bytes=256 << 20)
+    srv = fse.Server(ctx, arena_bytes=24 << 30, max_queue=4096, max_resident=256, max_batch=16)
+    outs = {}
+    tickets = []
+    done_count = [0]
+
+    def waiter():
+        i = 0
+        while i < n:
+            if i >= len(tickets):
+                time.sleep(0.0005)
+                continue
+            srv.wait(tickets[i], timeout_ms=120000)
+            outs.pop(i, None)
+            i += 1
+        done_count[0] = i
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.perf_counter()
+    t_meas = None
+    for k in range(n):
+        now = time.perf_counter() - t0
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        if k == n_warm:
+            t_meas = time.perf_counter()
+        job = pool[k % pool_size]
+        out = np.empty_like(job["image"])
+        outs[k] = out
+        tickets.append(srv.submit(job["image"], job["mask"], out, job["params"]))
+    th.join()
+    t_end = time.perf_counter()
+    lat = srv.latencies()[-n_measured:]
+    srv.close()
+    ctx.close()
+    px = sum(pool[k % pool_size]["image"].size for k in range(n_warm, n))
+    wall = t_end - t_meas
+    return {"requests": n_measured, "warmup_requests": n_warm, "offered_rate_hz": rate_hz,
+            "achieved_rate_hz": n_measured / wall, "mpix_per_s": px / wall / 1e6,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3),
+            "pool": f"{pool_size} seeded requests reused cyclically; Poisson arrivals drawn per request",
+            "lanes": 4}
 
 
 # ---------------------------------------------------------------------------
@@ -301,6 +365,10 @@ def main():
                "mpix_per_s": world * pix * args.steps / e2e_s / 1e6}
         e2e_ctx.close()
 
+    serving = None
+    if args.serve_requests > 0:
+        serving = serve_leg(fse, local, args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, dt, cores = oracle_blocks_per_s(jobs[0], args.cpu_seconds)
@@ -318,7 +386,8 @@ def main():
                 "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "mpix_per_s": mpix, "roofline": roof, "cpu_baseline": cpu,
-                "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps}
+                "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+                "serving": serving}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

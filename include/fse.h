@@ -188,10 +188,11 @@ int fse_extrapolate_host(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, v
 /* ---- serving: continuous batching ---------------------------------------- */
 typedef struct fse_server fse_server_t;
 typedef struct fse_server_cfg_t {
-    size_t arena_bytes;    /* device bytes for resident request state        */
-    int32_t max_queue;     /* pending requests before FSE_EBUSY              */
-    int32_t max_resident;  /* requests resident on the GPU at once           */
-    int32_t tick_items;    /* block budget per device tick (0 = automatic)   */
+    size_t arena_bytes;    /* device bytes for resident request state; cut into
+                              4 lanes, each running one batch at a time       */
+    int32_t max_queue;     /* pending requests before FSE_EBUSY (0 = 64)     */
+    int32_t max_resident;  /* requests resident on the GPU at once (0 = 64)  */
+    int32_t max_batch;     /* requests per lane launch (0 = 16)              */
 } fse_server_cfg_t;
 
 #define FSE_REQ_QUEUED 0
@@ -200,11 +201,16 @@ typedef struct fse_server_cfg_t {
 #define FSE_REQ_FAILED 3
 
 /*
- * fse_server_create -- starts the serving thread on the context's GPU.  The
- * server owns its own device memory (cfg->arena_bytes); the context's arena is
- * not used.  Requests are admitted while their estimated device bytes fit
- * the free memory, their image and mask stay resident until done, and blocks
- * of every resident request share each device tick.
+ * fse_server_create -- starts the serving thread on the context's GPU (the
+ * context supplies the device and its options; its arena is not used).  The
+ * server reserves cfg->arena_bytes of device memory (FSE_ENOMEM if that much
+ * is not free) in 4 lanes.  Continuous batching: whenever a lane is free, the
+ * queued requests that fit its device bytes (an upper-bound estimate per
+ * request) are admitted in arrival order and launched as one batch on the
+ * lane's stream; lanes run concurrently, so requests arriving while others are
+ * on the GPU start as soon as a lane frees up.  Every result equals the result
+ * of the same job run alone.  fse_server_destroy finishes queued and running
+ * requests first.
  */
 int fse_server_create(fse_server_t** srv, fse_context_t* ctx, const fse_server_cfg_t* cfg);
 /*

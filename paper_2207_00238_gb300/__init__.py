@@ -60,7 +60,7 @@ class Stats(ctypes.Structure):
 
 class ServerCfg(ctypes.Structure):
     _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_queue", ctypes.c_int32),
-                ("max_resident", ctypes.c_int32), ("tick_items", ctypes.c_int32)]
+                ("max_resident", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
 
 
 EXPORTS = ["fse_plan_tiles", "fse_context_create", "fse_context_destroy", "fse_context_set_option",
@@ -212,3 +212,52 @@ class Context:
 
     def wait_probe(self, timeout_us):
         return load().fse_debug_wait_probe(self.h, timeout_us)
+
+
+class Server:
+    """Continuous-batching request server (fse_server_*).  Host buffers."""
+
+    def __init__(self, ctx, arena_bytes=4 << 30, max_queue=256, max_resident=64, max_batch=16):
+        L = load()
+        h = ctypes.c_void_p()
+        cfg = ServerCfg(arena_bytes, max_queue, max_resident, max_batch)
+        _check(L.fse_server_create(ctypes.byref(h), ctx.h, ctypes.byref(cfg)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, image, mask, out, params, out_f32=None):
+        """image/mask/out: numpy uint8 arrays (out must stay alive until wait)."""
+        job = make_job(image, mask, out, params, out_f32=out_f32)
+        t = ctypes.c_uint64(0)
+        _check(load().fse_submit(self.h, ctypes.byref(job), ctypes.byref(t)))
+        self._keep[t.value] = (out, out_f32)
+        return t.value
+
+    def poll(self, ticket):
+        st = ctypes.c_int32(0)
+        _check(load().fse_poll(self.h, ticket, ctypes.byref(st)))
+        return st.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        st = Stats()
+        rc = load().fse_wait(self.h, ticket, timeout_ms, ctypes.byref(st))
+        if rc == OK:
+            self._keep.pop(ticket, None)
+        _check(rc)
+        return st.as_dict()
+
+    def latencies(self, cap=1 << 20):
+        buf = (ctypes.c_double * cap)()
+        n = _check(load().fse_server_latencies(self.h, buf, cap))
+        return np.frombuffer(buf, dtype=np.float64, count=n).copy()
+
+    def close(self):
+        if self.h:
+            load().fse_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

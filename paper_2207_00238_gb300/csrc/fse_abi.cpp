@@ -1,5 +1,6 @@
 // extern "C" entry points declared in include/fse.h.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -32,6 +33,70 @@ void tune_load(Context* c) {
     }
   }
   fclose(f);
+}
+
+// Copies host inputs into the arena front, runs the batch and copies the
+// outputs back, all enqueued on st (asynchronous for pinned host memory).
+int enqueue_host(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st,
+                 fse_stats_t* stats) {
+  if (!c) return fail(FSE_EINVAL, "NULL ctx");
+  if (n < 0 || (n > 0 && !jobs)) return fail(FSE_EINVAL, "bad job list");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(FSE_ECUDA, "cudaSetDevice");
+  std::vector<fse_job_t> dj(jobs, jobs + n);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = (off + 255) / 256 * 256; off = r + bytes; return r; };
+  for (int i = 0; i < n; ++i) {
+    int rc = check_job(jobs[i], i);
+    if (rc) return rc;
+    const size_t px = (size_t)jobs[i].W * jobs[i].H;
+    dj[i].image = (const uint8_t*)(c->arena + take(px));
+    dj[i].mask = (const uint8_t*)(c->arena + take(px));
+    dj[i].out = (uint8_t*)(c->arena + take(px));
+    dj[i].out_f32 = jobs[i].out_f32 ? (float*)(c->arena + take(px * 4)) : nullptr;
+    dj[i].out_f64 = jobs[i].out_f64 ? (double*)(c->arena + take(px * 8)) : nullptr;
+    dj[i].pitch = jobs[i].W;
+  }
+  off = (off + 255) / 256 * 256;
+  if (off >= c->arena_bytes) return fail(FSE_ENOMEM, "arena too small for the host path");
+  for (int i = 0; i < n; ++i) {
+    const fse_job_t& j = jobs[i];
+    cudaError_t e = cudaMemcpy2DAsync((void*)dj[i].image, j.W, j.image, j.pitch, j.W, j.H,
+                                      cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync((void*)dj[i].mask, j.W, j.mask, j.pitch, j.W, j.H,
+                            cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  }
+  int rc = run_batch(c, dj.data(), n, st, stats, off);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    const fse_job_t& j = jobs[i];
+    cudaError_t e = cudaMemcpy2DAsync(j.out, j.pitch, dj[i].out, j.W, j.W, j.H,
+                                      cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && j.out_f32)
+      e = cudaMemcpyAsync(j.out_f32, dj[i].out_f32, sizeof(float) * j.W * j.H,
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && j.out_f64)
+      e = cudaMemcpyAsync(j.out_f64, dj[i].out_f64, sizeof(double) * j.W * j.H,
+                          cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  }
+  return FSE_OK;
+}
+
+// Device bytes one job needs on the host-buffer path (inputs, outputs and the
+// planner's state), an upper bound used for admission.
+size_t job_device_bytes(const fse_job_t& j) {
+  const fse_params_t& p = j.p;
+  const size_t px = (size_t)j.W * j.H;
+  const double grow = 1.0 + 4.0 * p.overlap * std::sqrt((double)std::max(p.n_tiles, 1)) /
+                                std::max(1, std::min(j.W, j.H));
+  const size_t ext_px = (size_t)(px * std::min(grow, (double)std::max(p.n_tiles, 1)) + 1);
+  const size_t blocks = ext_px / ((size_t)p.block * p.block) + 4 * (size_t)p.n_tiles * (j.W + j.H) / p.block + 16;
+  const size_t vbytes = p.precision == 64 ? 8 : 4;
+  return px * 3 + (j.out_f32 ? 4 * px : 0) + (j.out_f64 ? 8 * px : 0) + ext_px * vbytes +
+         blocks * (4 + 8 + 4 + 4 + 4 * MAX_CLS) + (size_t)(p.block + 2 * p.border) * (p.block + 2 * p.border) * 12 +
+         (1 << 16);
 }
 
 }  // namespace fse
@@ -100,50 +165,9 @@ int fse_extrapolate_batch(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, 
 
 int fse_extrapolate_host(fse_context_t* c, const fse_job_t* jobs, int32_t n, void* cuda_stream,
                          fse_stats_t* stats) {
-  if (!c) return fse::fail(FSE_EINVAL, "NULL ctx");
-  if (n < 0 || (n > 0 && !jobs)) return fse::fail(FSE_EINVAL, "bad job list");
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  if (cudaSetDevice(c->device) != cudaSuccess) return fse::fail(FSE_ECUDA, "cudaSetDevice");
-  // device copies of image, mask, out (pitch W) and out_f32 at the arena front
-  std::vector<fse_job_t> dj(jobs, jobs + n);
-  size_t off = 0;
-  auto take = [&](size_t bytes) { size_t r = (off + 255) / 256 * 256; off = r + bytes; return r; };
-  for (int i = 0; i < n; ++i) {
-    int rc = fse::check_job(jobs[i], i);
-    if (rc) return rc;
-    const size_t px = (size_t)jobs[i].W * jobs[i].H;
-    dj[i].image = (const uint8_t*)(c->arena + take(px));
-    dj[i].mask = (const uint8_t*)(c->arena + take(px));
-    dj[i].out = (uint8_t*)(c->arena + take(px));
-    dj[i].out_f32 = jobs[i].out_f32 ? (float*)(c->arena + take(px * 4)) : nullptr;
-    dj[i].out_f64 = jobs[i].out_f64 ? (double*)(c->arena + take(px * 8)) : nullptr;
-    dj[i].pitch = jobs[i].W;
-  }
-  off = (off + 255) / 256 * 256;
-  if (off >= c->arena_bytes) return fse::fail(FSE_ENOMEM, "arena too small for the host path");
-  for (int i = 0; i < n; ++i) {
-    const fse_job_t& j = jobs[i];
-    cudaError_t e = cudaMemcpy2DAsync((void*)dj[i].image, j.W, j.image, j.pitch, j.W, j.H,
-                                      cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync((void*)dj[i].mask, j.W, j.mask, j.pitch, j.W, j.H,
-                            cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return fse::cuda_fail(e, "host-to-device copy");
-  }
-  int rc = fse::run_batch(c, dj.data(), n, st, stats, off);
+  int rc = fse::enqueue_host(c, jobs, n, st, stats);
   if (rc) return rc;
-  for (int i = 0; i < n; ++i) {
-    const fse_job_t& j = jobs[i];
-    cudaError_t e = cudaMemcpy2DAsync(j.out, j.pitch, dj[i].out, j.W, j.W, j.H,
-                                      cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && j.out_f32)
-      e = cudaMemcpyAsync(j.out_f32, dj[i].out_f32, sizeof(float) * j.W * j.H,
-                          cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && j.out_f64)
-      e = cudaMemcpyAsync(j.out_f64, dj[i].out_f64, sizeof(double) * j.W * j.H,
-                          cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return fse::cuda_fail(e, "device-to-host copy");
-  }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fse::cuda_fail(e, "cudaStreamSynchronize");
   return FSE_OK;

@@ -125,7 +125,8 @@ static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; 
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
-int context_create(Context** out, int device, size_t arena_bytes, const char* tune_path) {
+static int context_init(Context** out, int device, size_t arena_bytes, char* alias,
+                        const char* tune_path) {
   *out = nullptr;
   int ndev = 0;
   FSE_CUDA(cudaGetDeviceCount(&ndev));
@@ -138,11 +139,16 @@ int context_create(Context** out, int device, size_t arena_bytes, const char* tu
   cudaError_t e = cudaGetDeviceProperties(&prop, device);
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDeviceProperties"); }
   c->sm_count = prop.multiProcessorCount;
-  e = cudaMalloc(&c->arena, arena_bytes);
-  if (e != cudaSuccess) {
-    delete c;
-    cudaGetLastError();
-    return fail(FSE_ENOMEM, "cudaMalloc(%zu) for the arena failed", arena_bytes);
+  if (alias) {
+    c->arena = alias;
+    c->owns_arena = false;
+  } else {
+    e = cudaMalloc(&c->arena, arena_bytes);
+    if (e != cudaSuccess) {
+      delete c;
+      cudaGetLastError();
+      return fail(FSE_ENOMEM, "cudaMalloc(%zu) for the arena failed", arena_bytes);
+    }
   }
   c->arena_bytes = arena_bytes;
   float2 twf[64];
@@ -177,11 +183,19 @@ int context_create(Context** out, int device, size_t arena_bytes, const char* tu
   return FSE_OK;
 }
 
+int context_create(Context** out, int device, size_t arena_bytes, const char* tune_path) {
+  return context_init(out, device, arena_bytes, nullptr, tune_path);
+}
+
+int context_create_alias(Context** out, int device, char* arena, size_t arena_bytes) {
+  return context_init(out, device, arena_bytes, arena, nullptr);
+}
+
 void context_destroy(Context* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-  if (c->arena) cudaFree(c->arena);
+  if (c->arena && c->owns_arena) cudaFree(c->arena);
   if (c->host_buf) cudaFreeHost(c->host_buf);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);

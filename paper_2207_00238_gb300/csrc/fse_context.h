@@ -15,6 +15,7 @@ struct fse_context {
   int sm_count = 0;
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  bool owns_arena = true;
   char* host_buf = nullptr;  // pinned staging of the per-call tables
   size_t host_cap = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
@@ -53,6 +54,10 @@ int plan_tiles(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out, int3
                int32_t* n_out);
 int check_job(const fse_job_t& j, int idx);
 int context_create(Context** out, int device, size_t arena_bytes, const char* tune_path);
+// A context on caller-owned device memory (not freed by context_destroy).
+int context_create_alias(Context** out, int device, char* arena, size_t arena_bytes);
+int enqueue_host(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse_stats_t* stats);
+size_t job_device_bytes(const fse_job_t& j);
 void context_destroy(Context* c);
 int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse_stats_t* stats,
               size_t arena_offset);

@@ -81,16 +81,23 @@ def _to_u8(x):
 def image(W, H, rng, structure=False):
     """128 + linear gradient + 6 random 2-D sinusoids (+ 8 rectangles and 4 step
     edges when ``structure``) + Gaussian noise sigma=2, clipped and rounded."""
-    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    xs = np.arange(W, dtype=np.float64)
+    ys = np.arange(H, dtype=np.float64)
     gx = rng.uniform(1, -32, 32)[0] / W
     gy = rng.uniform(1, -32, 32)[0] / H
-    img = 128.0 + gx * (x - W / 2) + gy * (y - H / 2)
+    img = 128.0 + gx * (xs[None, :] - W / 2) + gy * (ys[:, None] - H / 2)
     a = rng.uniform(6, 8, 24)
     fx = rng.uniform(6, -0.15, 0.15)
     fy = rng.uniform(6, -0.15, 0.15)
     ph = rng.uniform(6, 0, 2 * math.pi)
     for i in range(6):
-        img += a[i] * np.cos(2 * math.pi * (fx[i] * x + fy[i] * y) + ph[i])
+        # a cos(2 pi (fx x + fy y) + ph), evaluated separably
+        cx, sx = np.cos(2 * math.pi * fx[i] * xs), np.sin(2 * math.pi * fx[i] * xs)
+        cy = np.cos(2 * math.pi * fy[i] * ys + ph[i])
+        sy = np.sin(2 * math.pi * fy[i] * ys + ph[i])
+        img += a[i] * (cy[:, None] * cx[None, :] - sy[:, None] * sx[None, :])
+    y = ys[:, None]
+    x = xs[None, :]
     if structure:
         for _ in range(8):
             rw = int(round(rng.uniform(1, 0.05, 0.30)[0] * W))
