@@ -185,6 +185,33 @@ int fse_extrapolate_batch(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, 
 int fse_extrapolate_host(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void* cuda_stream,
                          fse_stats_t* stats);
 
+/*
+ * fse_extrapolate_noalloc -- the pass of fse_extrapolate_batch for callers that
+ * cannot allocate device memory (the paper has no counterpart; this is a
+ * library convenience).  Such callers include plug-ins whose host application
+ * owns the device-memory budget and latency-bound loops that must not call
+ * cudaMalloc, which can synchronize the device.  The call allocates nothing:
+ * all scratch state lives in one array of FSE_NOALLOC_SCRATCH_BYTES of device
+ * memory declared statically in the library (every GPU that loads the library
+ * holds it until the process exits), the tables are staged in static host
+ * arrays, and no context is needed.
+ *   jobs[i].image/mask/out/out_f32/out_f64: DEVICE pointers of the current
+ *   device (cudaSetDevice), as for fse_extrapolate_batch; at most 16 jobs and
+ *   1024 tiles per call.
+ *   cuda_stream: the stream the work is ordered on (NULL = default stream);
+ *   the call returns after that work has finished.
+ * The first call on a device sets that device up (looks up the scratch
+ * array's device address, uploads constants, configures the kernels); make it
+ * before any stream capture.  Every call shares the one scratch array and
+ * clears what must start empty; calls that overlapped on the GPU would race,
+ * so calls are serialized by a process-wide lock.
+ * Errors: FSE_ENOMEM when the call needs more than FSE_NOALLOC_SCRATCH_BYTES of
+ * scratch (the message says how much), FSE_EINVAL for bad jobs or more than
+ * 16 jobs / 1024 tiles, FSE_EDEGENERATE, FSE_ETIMEOUT, FSE_ECUDA.
+ */
+#define FSE_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int fse_extrapolate_noalloc(const fse_job_t* jobs, int32_t n, void* cuda_stream);
+
 /* ---- serving: continuous batching ---------------------------------------- */
 typedef struct fse_server fse_server_t;
 typedef struct fse_server_cfg_t {

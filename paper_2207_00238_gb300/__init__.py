@@ -66,7 +66,8 @@ class ServerCfg(ctypes.Structure):
 EXPORTS = ["fse_plan_tiles", "fse_context_create", "fse_context_destroy", "fse_context_set_option",
            "fse_extrapolate_batch", "fse_extrapolate_host", "fse_server_create", "fse_submit",
            "fse_poll", "fse_wait", "fse_server_latencies", "fse_server_destroy", "fse_last_error",
-           "fse_debug_fetch", "fse_debug_wait_probe", "fse_context_kernel_times"]
+           "fse_debug_fetch", "fse_debug_wait_probe", "fse_context_kernel_times",
+           "fse_extrapolate_noalloc"]
 
 _lib = None
 
@@ -99,6 +100,7 @@ def load(path=LIB_PATH):
     L.fse_debug_fetch.argtypes = [vp, P(i32), P(i32), i32, P(i32)]
     L.fse_debug_fetch.restype = i32
     L.fse_debug_wait_probe.argtypes = [vp, i32]
+    L.fse_extrapolate_noalloc.argtypes = [P(Job), i32, vp]
     L.fse_context_kernel_times.argtypes = [vp, P(ctypes.c_float), i32]
     L.fse_context_kernel_times.restype = i32
     _lib = L
@@ -123,6 +125,14 @@ def plan_tiles(W, H, N, d):
     _check(L.fse_plan_tiles(W, H, N, d, arr, max(N, 1), ctypes.byref(n)))
     return np.array([[getattr(arr[i], f) for f, _ in Tile._fields_] for i in range(n.value)],
                     np.int32).reshape(-1, 8)
+
+
+def extrapolate_noalloc(jobs, stream=None):
+    """fse_extrapolate_noalloc: the batch pass without any allocation, for
+    callers that cannot allocate device memory.  Device pointers of the
+    current device; returns once the work on `stream` has finished."""
+    arr = (Job * len(jobs))(*jobs)
+    _check(load().fse_extrapolate_noalloc(arr, len(jobs), stream))
 
 
 def make_params(block, border, fft, K, rho=0.8, delta=0.5, gamma=0.5, order="phased",

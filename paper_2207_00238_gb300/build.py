@@ -16,7 +16,7 @@ LIB = os.path.join(OUT_DIR, "libfse.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SRC = ["fse_kernels.cu"]
+CU_SRC = ["fse_kernels.cu", "fse_noalloc.cu"]
 CPP_SRC = ["fse_api.cpp", "fse_abi.cpp", "fse_server.cpp"]
 
 
