@@ -60,6 +60,10 @@ def workload(name):
 
 def describe(name, jobs):
     p = jobs[0]["params"]
+    if len(jobs) > 1:
+        return {"workload": name, "images": len(jobs), "pixels": int(sum(j["image"].size for j in jobs)),
+                "blocks": sorted({j["params"]["block"] for j in jobs}),
+                "fft": sorted({j["params"]["fft"] for j in jobs}), "order": p["order"]}
     d = {"workload": name, "images": len(jobs),
          "size": f"{jobs[0]['image'].shape[1]}x{jobs[0]['image'].shape[0]}" if len(jobs) == 1 else "mixed",
          "block": p["block"], "border": p["border"], "fft": p["fft"], "K": p["K"],
@@ -329,7 +333,9 @@ def main():
     achieved = bins * BYTES_PER_BIN_ITER / (kmean / 1000.0) / 1e9
     roof = {"bound": "alu", "pipe": "shared-memory (LSU) pipe, 128 B/clk/SM",
             "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
-            "traffic": None, "kernel": "k_exec_f32_64" if jobs[0]["params"]["fft"] == 64 else "k_exec_f32_32",
+            "traffic": None,
+            "kernel": "+".join(sorted({"k_exec_f32_64" if j["params"]["fft"] == 64 else "k_exec_f32_32"
+                                       for j in jobs})),
             "kernel_ms": kmean, "bin_iterations_per_launch": bins,
             "peak_basis": f"derived: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {sms} SMs x {f_max:.0f} MHz"}
     if clk:
