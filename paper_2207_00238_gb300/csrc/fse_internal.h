@@ -48,23 +48,19 @@ struct TileDev {
   int64_t val_off;  // first pixel of this tile's value plane (elements)
 };
 
-// Per-class ready queue with priority levels: an item is pushed into the
-// queue of its level (its PHASED phase, capped) once every block it depends on
-// is done; consumers claim an already-pushed item from the lowest non-empty
-// level.  Level l owns slots [sum of lcnt below l, + lcnt[l]).
-constexpr int NLEV = 32;
+// Per-class ready queue: an item is pushed once every block it depends on is
+// done; a consumer reserves the next slot with one atomicAdd and waits
+// (bounded by a progress watchdog) until that slot's item is pushed.  Slots
+// are reserved in push order, so every pushed item has a consumer.
 struct QueueDev {
   int32_t n_items;  // items of this class (written by the planner)
-  int32_t claimed;  // items handed to consumers
+  int32_t head;     // next slot to reserve
+  int32_t tail;     // next slot to push
   int32_t n_done;   // items finished (progress watchdog of waiting consumers)
   int32_t n_empty;
   int32_t n_core;   // lost blocks that touch their tile's core
   int32_t error;    // ErrBits
   int32_t error_info;
-  int32_t pad;
-  int32_t lcnt[NLEV];   // items per level
-  int32_t lhead[NLEV];  // claimed per level
-  int32_t ltail[NLEV];  // pushed per level
 };
 
 struct ClassArgs {

@@ -67,89 +67,47 @@ __device__ __forceinline__ int64_t order_key(const JobDev& J, int I, int Jb) {
   return k;
 }
 
-// Priority level of an item: its PHASED phase (capped), 0 for other orders.
-__device__ __forceinline__ int item_level(const JobDev& J, int I, int Jb) {
-  if (J.order != ORDER_PHASED) return 0;
-  return min((I % J.P) * J.P + (Jb % J.P), NLEV - 1);
+__device__ __forceinline__ void queue_push(const ClassArgs& C, int item) {
+  const int pos = atomicAdd(&C.q->tail, 1);
+  st_release(&C.slots[pos], item);
 }
 
-// First slot of level l: levels are laid out one after another.
-__device__ __forceinline__ int level_offset(const QueueDev* q, int l) {
-  int o = 0;
-  for (int k = 0; k < l; ++k) o += __ldcg(&q->lcnt[k]);
-  return o;
-}
-
-__device__ __forceinline__ void queue_push(const ClassArgs& C, int item, int lvl) {
-  const int pos = atomicAdd(&C.q->ltail[lvl], 1);
-  st_release(&C.slots[level_offset(C.q, lvl) + pos], item);
-}
-
-// Warp-cooperative pop (all 32 lanes call it): claims a pushed item from the
-// lowest non-empty level.  Returns the item id, -1 once every item has been
-// claimed, -2 on error.  A waiting warp gives up with ERR_TIMEOUT when no item
-// of the class finished for timeout_ns (progress watchdog, wall clock).
+// Warp-cooperative pop (all 32 lanes call it): lane 0 reserves the next slot
+// and waits for its item.  Returns the item id, -1 once every item has been
+// reserved, -2 on error.  A waiting warp gives up with ERR_TIMEOUT when no
+// item of the class finished for timeout_ns (progress watchdog, wall clock).
 __device__ int queue_pop_warp(const ClassArgs& C, int64_t timeout_ns, int lane) {
-  QueueDev* q = C.q;
-  const int n = __shfl_sync(0xffffffffu, min(ld_relaxed(&q->n_items), C.cap), 0);
-  int last_done = -1;
-  unsigned long long t_last = 0;
-  unsigned sleep_ns = 64;
-  for (;;) {
-    const int h = ld_relaxed(&q->lhead[lane]);
-    const int tl = ld_relaxed(&q->ltail[lane]);
-    const unsigned avail = __ballot_sync(0xffffffffu, h < tl);
-    if (avail) {
-      const int l = __ffs(avail) - 1;
-      int pos = -1;
-      if (lane == l && atomicCAS(&q->lhead[l], h, h + 1) == h) pos = h;
-      pos = __shfl_sync(0xffffffffu, pos, l);
-      if (pos < 0) continue;  // another consumer won this slot: rescan
-      int item = 0;
-      if (lane == 0) {
-        // the producer bumped ltail just before writing the slot
-        int* slot = &C.slots[level_offset(q, l) + pos];
-        const uint64_t t0 = global_ns();
-        while ((item = ld_acquire(slot)) < 0) {
-          if ((int64_t)(global_ns() - t0) > timeout_ns) {
-            atomicOr(&q->error, ERR_TIMEOUT);
-            q->error_info = pos;
-            item = -2;
-            break;
-          }
+  int item = -1;
+  if (lane == 0) {
+    QueueDev* q = C.q;
+    const int n = min(ld_relaxed(&q->n_items), C.cap);
+    const int pos = atomicAdd(&q->head, 1);
+    if (pos < n) {
+      int last_done = ld_relaxed(&q->n_done);
+      uint64_t t_last = global_ns();
+      unsigned sleep_ns = 32;
+      while ((item = ld_acquire(&C.slots[pos])) < 0) {
+        if (ld_relaxed(&q->error) != 0) {
+          item = -2;
+          break;
         }
-        if (item >= 0) atomicAdd(&q->claimed, 1);
+        const int done = ld_relaxed(&q->n_done);
+        const uint64_t now = global_ns();
+        if (done != last_done) {
+          last_done = done;
+          t_last = now;
+        } else if ((int64_t)(now - t_last) > timeout_ns) {
+          atomicOr(&q->error, ERR_TIMEOUT);
+          q->error_info = pos;
+          item = -2;
+          break;
+        }
+        __nanosleep(sleep_ns);
+        if (sleep_ns < 1024) sleep_ns <<= 1;
       }
-      return __shfl_sync(0xffffffffu, item, 0);
     }
-    // every exit decision is taken on lane 0's reads, broadcast to the warp
-    int claimed = 0, err = 0, done = 0;
-    unsigned long long now = 0;
-    if (lane == 0) {
-      claimed = ld_relaxed(&q->claimed);
-      err = ld_relaxed(&q->error);
-      done = ld_relaxed(&q->n_done);
-      now = global_ns();
-    }
-    claimed = __shfl_sync(0xffffffffu, claimed, 0);
-    err = __shfl_sync(0xffffffffu, err, 0);
-    done = __shfl_sync(0xffffffffu, done, 0);
-    now = __shfl_sync(0xffffffffu, now, 0);
-    if (claimed >= n) return -1;
-    if (err != 0) return -2;
-    if (done != last_done) {
-      last_done = done;
-      t_last = now;
-    } else if ((int64_t)(now - t_last) > timeout_ns) {
-      if (lane == 0) {
-        atomicOr(&q->error, ERR_TIMEOUT);
-        q->error_info = -1;
-      }
-      return -2;
-    }
-    __nanosleep(sleep_ns);
-    if (sleep_ns < 1024) sleep_ns <<= 1;
   }
+  return __shfl_sync(0xffffffffu, item, 0);
 }
 
 // After a block's writes are globally visible: decrement the pending count
@@ -167,7 +125,7 @@ __device__ __forceinline__ void release_successors(const ExecArgs& a, const Clas
     if (id2 < 0 || order_key(J, I2, J2) <= kx) continue;
     if (atomicSub(&C.cnt[id2], 1) == 1) {
       __threadfence();
-      queue_push(C, id2, item_level(J, I2, J2));
+      queue_push(C, id2);
     }
   }
 }
@@ -206,29 +164,49 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
     delta = J.delta;
   }
   const bool use_done = J.order != ORDER_INDEPENDENT;
-  for (int e = t; e < S * S; e += nthr) {
-    const int m = e / S, n = e - m * S;
-    real wv = 0, zr = 0;
-    const int ty = oy + m, tx = ox + n;
-    if (ty >= 0 && ty < T.eh && tx >= 0 && tx < T.ew) {
-      // independent loads first (mask, pixel, value plane), then combine
-      const size_t gi = (size_t)(T.ey + ty) * J.pitch + (T.ex + tx);
-      const real wi = __ldg(wiso + e);
-      const uint8_t mk = __ldg(J.mask + gi);
-      const real px = (real)__ldg(J.image + gi);
-      const real v = __ldcg(val + (size_t)ty * T.ew + tx);
-      if (mk == 0) {
-        wv = wi;
-        zr = wi * px;
-      } else if (use_done && !isnan(v)) {
-        wv = delta * wi;
-        zr = wv * v;
+  constexpr int U = 4;  // pixels per thread whose loads are in flight together
+  for (int e0 = t; e0 < S * S; e0 += U * nthr) {
+    uint8_t mk[U], px[U];
+    real wi[U], v[U];
+    bool in[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {  // all loads first
+      const int e = e0 + u * nthr;
+      const int m = e / S, n = e - m * S;
+      const int ty = oy + m, tx = ox + n;
+      in[u] = e < S * S && ty >= 0 && ty < T.eh && tx >= 0 && tx < T.ew;
+      mk[u] = 1;
+      px[u] = 0;
+      wi[u] = 0;
+      v[u] = 0;
+      if (in[u]) {
+        const size_t gi = (size_t)(T.ey + ty) * J.pitch + (T.ex + tx);
+        wi[u] = __ldg(wiso + e);
+        mk[u] = __ldg(J.mask + gi);
+        px[u] = __ldg(J.image + gi);
+        v[u] = __ldcg(val + (size_t)ty * T.ew + tx);
       }
     }
-    real2 z;
-    z.x = wv;
-    z.y = zr;
-    zbuf[swz<F>(m, n)] = z;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * nthr;
+      if (e >= S * S) break;
+      const int m = e / S, n = e - m * S;
+      real wv = 0, zr = 0;
+      if (in[u]) {
+        if (mk[u] == 0) {
+          wv = wi[u];
+          zr = wi[u] * (real)px[u];
+        } else if (use_done && !isnan(v[u])) {
+          wv = delta * wi[u];
+          zr = wv * v[u];
+        }
+      }
+      real2 z;
+      z.x = wv;
+      z.y = zr;
+      zbuf[swz<F>(m, n)] = z;
+    }
   }
 }
 
@@ -1170,7 +1148,6 @@ __global__ void k_mark(const __grid_constant__ ExecArgs a) {
       id = atomicAdd(&C.q->n_items, 1);
       if (id < C.cap) {
         C.items[id] = make_int2(blockIdx.y, (I << 16) | Jb);
-        atomicAdd(&C.q->lcnt[item_level(J, I, Jb)], 1);
         if (core) atomicAdd(&C.q->n_core, 1);
       } else {
         atomicOr(&C.q->error, ERR_BOUNDS);
@@ -1206,7 +1183,7 @@ __global__ void k_deps(const __grid_constant__ ExecArgs a, int cls) {
     C.cnt[id] = cnt;
     if (a.level_of) a.level_of[(size_t)cls * a.level_stride + id] =
         J.order == ORDER_PHASED ? (I % J.P) * J.P + (Jb % J.P) : 0;
-    if (cnt == 0) queue_push(C, id, item_level(J, I, Jb));
+    if (cnt == 0) queue_push(C, id);
   }
 }
 
