@@ -62,6 +62,9 @@ def lib():
                                           P(ctypes.c_uint8), P(f64), P(_BlkReport), P(i32), i32,
                                           P(i32), i32, i32, ctypes.c_int64, P(ctypes.c_int64)]
         _lib.oracle_threads.restype = ctypes.c_int
+        _lib.oracle_fse_block_alone.restype = f64
+        _lib.oracle_fse_block_alone.argtypes = [P(ctypes.c_uint8), P(ctypes.c_uint8)] + [i32] * 10 + \
+            [f64, f64, f64, i32, i32, P(f64)]
     return _lib
 
 
@@ -110,6 +113,22 @@ def fse_model(c, m, n):
     cre = np.ascontiguousarray(c.real.ravel(), np.float64)
     cim = np.ascontiguousarray(c.imag.ravel(), np.float64)
     return lib().oracle_fse_model(_ptr(cre, ctypes.c_double), _ptr(cim, ctypes.c_double), F, m, n)
+
+
+def fse_block_alone(img, mask, tile, I, J, *, block, border, fft, K, rho=0.8, gamma=0.5,
+                    tau=1e-9, **_):
+    """One block (I, J) of extended tile `tile` (x, y, w, h, ex, ey, ew, eh) with
+    all lost pixels pending -- what a PHASED phase-0 block sees.  Returns
+    (W0, g[b, b])."""
+    img = np.ascontiguousarray(img, np.uint8)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    H, W = img.shape
+    g = np.zeros(block * block)
+    ex, ey, ew, eh = (int(v) for v in tile[4:8])
+    W0 = lib().oracle_fse_block_alone(_ptr(img, ctypes.c_uint8), _ptr(mask, ctypes.c_uint8), W, H,
+                                      ex, ey, ew, eh, block, border, fft, K, rho, gamma, tau,
+                                      I, J, _ptr(g, ctypes.c_double))
+    return W0, g.reshape(block, block)
 
 
 def fse_image(img, mask, *, block, border, fft, K, rho=0.8, delta=0.5, gamma=0.5,

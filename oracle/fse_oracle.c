@@ -435,6 +435,46 @@ int oracle_fse_image(const uint8_t *img, const uint8_t *mask, int32_t W, int32_t
     return OR_OK;
 }
 
+/*
+ * One block of one extended tile computed alone, with every lost pixel of the
+ * tile still pending (no earlier reconstruction in its support).  Under the
+ * PHASED order this is exactly what a phase-0 block sees, so sampled outputs of
+ * a full-size run can be checked block by block.
+ *   (ex, ey, ew, eh): the extended tile;  (I, J): the block in its grid.
+ *   g[b*b]: model values at the block's pixels (row-major, unrounded).
+ * Returns W0 (0: empty support, g set to 0).
+ */
+double oracle_fse_block_alone(const uint8_t *img, const uint8_t *mask, int32_t W, int32_t H,
+                              int32_t ex, int32_t ey, int32_t ew, int32_t eh, int32_t b, int32_t B,
+                              int32_t F, int32_t K, double rho, double gamma, double tau,
+                              int32_t I, int32_t J, double *g) {
+    (void)H;
+    const int S = b + 2 * B;
+    double *w = malloc(sizeof(double) * S * S), *r = malloc(sizeof(double) * S * S);
+    double *cre = malloc(sizeof(double) * F * F), *cim = malloc(sizeof(double) * F * F);
+    const double mc = B + (b - 1) / 2.0;
+    for (int m = 0; m < S; m++)
+        for (int n = 0; n < S; n++) {
+            int y = I * b - B + m, x = J * b - B + n;
+            double wv = 0, rv = 0;
+            if (y >= 0 && y < eh && x >= 0 && x < ew) {
+                int64_t gi = (int64_t)(ey + y) * W + (ex + x);
+                if (!mask[gi]) {
+                    wv = pow(rho, sqrt((m - mc) * (m - mc) + (n - mc) * (n - mc)));
+                    rv = (double)img[gi];
+                }
+            }
+            w[m * S + n] = wv;
+            r[m * S + n] = rv;
+        }
+    double W0 = oracle_fse_fit(w, r, NULL, S, F, K, gamma, tau, NULL, cre, cim, NULL, NULL, NULL);
+    for (int yy = 0; yy < b; yy++)
+        for (int xx = 0; xx < b; xx++)
+            g[yy * b + xx] = W0 > 0 ? oracle_fse_model(cre, cim, F, B + yy, B + xx) : 0.0;
+    free(w); free(r); free(cre); free(cim);
+    return W0;
+}
+
 int oracle_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -193,3 +193,26 @@ def test_invalid_params(oracle_lib):
         kw = dict(block=4, border=4, fft=16, K=4)
         kw.update(b)
         assert oracle_lib.fse_image(img, img, **kw)["rc"] == -1
+
+
+def test_block_alone_equals_phase0_blocks_of_whole_image(oracle_lib):
+    """The single-block routine reproduces the whole-image run on every block
+    of phase 0 (no earlier reconstruction inside its support)."""
+    img, mask = _tiny_case(21, 70, 54, 4, 0.3)
+    kw = dict(block=4, border=6, fft=16, K=15, rho=0.75, gamma=0.6)
+    res = oracle_lib.fse_image(img, mask, n_tiles=3, overlap=6, delta=0.5, report=True, **kw)
+    _, tiles = oracle_lib.plan_tiles(70, 54, 3, 6)
+    P = -(-6 // 4) + 1
+    n = 0
+    for t, I, J, _ in res["blocks"]:
+        if (I % P) * P + (J % P) != 0:
+            continue
+        x, y, w, h, ex, ey, ew, eh = tiles[t]
+        _, g = oracle_lib.fse_block_alone(img, mask, tiles[t], int(I), int(J), **kw)
+        for yy in range(4):
+            for xx in range(4):
+                gy, gx = ey + I * 4 + yy, ex + J * 4 + xx
+                if gy < ey + eh and gx < ex + ew and mask[gy, gx] and x <= gx < x + w and y <= gy < y + h:
+                    assert abs(res["g"][gy, gx] - g[yy, xx]) < 1e-9
+                    n += 1
+    assert n > 20
