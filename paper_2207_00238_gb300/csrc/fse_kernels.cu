@@ -587,20 +587,23 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
   const float gs = J.gamma_f / W0;
   float2(&R)[32] = x;
 
-  const uint32_t kmask = opaque(0xFFFFFC00u);
+  // key: energy bits with the low 5 bits replaced by 31 - row; ties between
+  // lanes (equal keys) go to the lowest lane, i.e. the lowest flat index
+  const uint32_t kmask = opaque(0xFFFFFFE0u);
   uint32_t bq[2] = {0u, 0u};  // two independent max chains, three-input max
   static_for<0, 16>([&](auto h) {
     constexpr int j = 2 * decltype(h)::value;
     const float e0 = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
     const float e1 = fmaf(R[j + 1].y, R[j + 1].y, R[j + 1].x * R[j + 1].x);
-    bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<(31u - j) << 5>(e0, kmask),
-                             make_key<(30u - j) << 5>(e1, kmask));
+    bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<31u - j>(e0, kmask),
+                             make_key<30u - j>(e1, kmask));
   });
-  uint32_t best = max(bq[0], bq[1]) | (uint32_t)(31 - lane);
+  uint32_t best = max(bq[0], bq[1]);
   for (int iter = 0; iter < K; ++iter) {
-    best = __reduce_max_sync(0xffffffffu, best);
-    const int flat = 1023 - (int)(best & 1023u);
-    const int u1 = flat >> 5, u2 = flat & 31;
+    const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
+    const int u2 = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
+    const int u1 = 31 - (int)(wbest & 31u);
+    const int flat = u1 * 32 + u2;
     const float2 v = select_reg<32>(R, u1);
     const float rux = __shfl_sync(0xffffffffu, v.x, u2);
     const float ruy = __shfl_sync(0xffffffffu, v.y, u2);
@@ -626,10 +629,10 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
         R[j + k] = make_float2(rx, ry);
         e[k] = fmaf(ry, ry, rx * rx);
       }
-      bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<(31u - j) << 5>(e[0], kmask),
-                               make_key<(30u - j) << 5>(e[1], kmask));
+      bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<31u - j>(e[0], kmask),
+                               make_key<30u - j>(e[1], kmask));
     });
-    best = max(bq[0], bq[1]) | (uint32_t)(31 - lane);
+    best = max(bq[0], bq[1]);
   }
   __syncwarp();
   if (a.dbg_useq)
@@ -685,7 +688,7 @@ struct alignas(16) CtaSmem64 {
   int32_t coef_u[KMAX];
   float2 tw[64];
   float red[NWB * 32];
-  alignas(16) float4 xrec[2][NWB];  // per warp: (key bits, 0, Re R_u, Im R_u)
+  alignas(16) float4 xrec[2][NWB];  // per warp: (key bits, flat bits, Re R_u, Im R_u)
   int item;
   TileDev T;
   JobDev J;
@@ -809,38 +812,42 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   }
   const float gs = J.gamma_f / W0;
   // key = energy bits, low 12 bits replaced by 4095 - flat; flat = k1*64 + c
-  const uint32_t kmask = opaque(0xFFFFF000u);
-  const uint32_t tbits = (uint32_t)(((NQ - 1 - q) * RPT) << 6) | (uint32_t)(63 - c);
+  // key: energy bits with the low log2(RPT) bits replaced by RPT-1-row; equal
+  // keys are resolved by the lowest flat index (lane ballot, then warps)
+  const uint32_t kmask = opaque(~(uint32_t)(RPT - 1));
 
   uint32_t bq[2] = {0u, 0u};
   static_for<0, RPT / 2>([&](auto h) {
     constexpr int i = 2 * decltype(h)::value;
     const float e0 = fmaf(R[i].y, R[i].y, R[i].x * R[i].x);
     const float e1 = fmaf(R[i + 1].y, R[i + 1].y, R[i + 1].x * R[i + 1].x);
-    bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i) << 6>(e0, kmask),
-                             make_key<(uint32_t)(RPT - 2 - i) << 6>(e1, kmask));
+    bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i)>(e0, kmask),
+                             make_key<(uint32_t)(RPT - 2 - i)>(e1, kmask));
   });
-  uint32_t best = max(bq[0], bq[1]) | tbits;
+  uint32_t best = max(bq[0], bq[1]);
   for (int iter = 0; iter < K; ++iter) {
-    best = __reduce_max_sync(0xffffffffu, best);
     {
-      const int flat = 4095 - (int)(best & 4095u);
-      const int i_w = (flat >> 6) % RPT, l_w = flat & 31;
+      const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
+      const int l_w = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
+      const int i_w = RPT - 1 - (int)(wbest & (uint32_t)(RPT - 1));
+      const int tw = (warp << 5) | l_w;  // the winning thread
+      const int flat_w = (i_w + RPT * (tw >> 6)) * 64 + (tw & 63);
       float2 v = select_reg<RPT>(R, i_w);
       v.x = __shfl_sync(0xffffffffu, v.x, l_w);
       v.y = __shfl_sync(0xffffffffu, v.y, l_w);
-      if (lane == 0) sm.xrec[iter & 1][warp] = make_float4(__uint_as_float(best), 0.f, v.x, v.y);
+      if (lane == 0)
+        sm.xrec[iter & 1][warp] = make_float4(__uint_as_float(wbest), __int_as_float(flat_w), v.x, v.y);
     }
     __syncthreads();
-    // largest key over the warps, carrying its R_u (one shared-memory round trip)
+    // largest key over the warps (lowest flat index on equal keys), carrying R_u
     float4 rb = sm.xrec[iter & 1][0];
 #pragma unroll
     for (int w = 1; w < NWB; ++w) {
       const float4 rw = sm.xrec[iter & 1][w];
-      if (__float_as_uint(rw.x) > __float_as_uint(rb.x)) rb = rw;
+      const uint32_t kw = __float_as_uint(rw.x), kb0 = __float_as_uint(rb.x);
+      if (kw > kb0 || (kw == kb0 && __float_as_int(rw.y) < __float_as_int(rb.y))) rb = rw;
     }
-    const uint32_t kb = __float_as_uint(rb.x);
-    const int flat = 4095 - (int)(kb & 4095u);
+    const int flat = __float_as_int(rb.y);
     const int u1 = flat >> 6, u2 = flat & 63;
     const float2 ru = make_float2(rb.z, rb.w);
     const float dx = gs * ru.x, dy = gs * ru.y;
@@ -867,10 +874,10 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
         R[i + k] = make_float2(rx, ry);
         e[k] = fmaf(ry, ry, rx * rx);
       }
-      bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i) << 6>(e[0], kmask),
-                               make_key<(uint32_t)(RPT - 2 - i) << 6>(e[1], kmask));
+      bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i)>(e[0], kmask),
+                               make_key<(uint32_t)(RPT - 2 - i)>(e[1], kmask));
     });
-    best = max(bq[0], bq[1]) | tbits;
+    best = max(bq[0], bq[1]);
   }
   __syncthreads();
   if (a.dbg_useq)
