@@ -14,11 +14,18 @@ import pytest
 
 import paper_2207_00238_gb300 as fse
 from paper_2207_00238_gb300 import synth
-from tests.gpu_util import run_gpu
+from tests.gpu_util import oracle_run, psnr, run_gpu
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1.0  # FP32 path: grey levels
+# At F = 64 with K = 200, late iterations select among residual bins whose
+# FP32 values carry rounding accumulated from the early, large updates; near-tied
+# selections then differ from FP64 and the extrapolated pixels move by a few grey
+# levels (0.4 % of the lost pixels of the 1024^2 workload, PSNR change 5e-4 dB).
+# The FP64 device path shows the arithmetic itself is exact (1e-9 gates below).
+TOL_F64_K200 = 4.0
+TOL_FP64 = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +63,7 @@ def _count_and_sample(oracle_lib, job, n_sample, seed):
     return total, tiles, [cand[i] for i in sorted(pick)]
 
 
-def _check_job(oracle_lib, job, got, lost_blocks, n_sample=32, seed=0):
+def _check_job(oracle_lib, job, got, lost_blocks, n_sample=32, seed=0, tol=None):
     img, mask, p = job["image"], job["mask"], job["params"]
     lost = mask > 0
     assert (got["out"][~lost] == img[~lost]).all()
@@ -84,14 +91,27 @@ def _check_job(oracle_lib, job, got, lost_blocks, n_sample=32, seed=0):
     with ThreadPoolExecutor(8) as ex:
         worst = max(ex.map(one, sample))
     assert len(sample) > 0
-    assert worst <= TOL, f"worst sampled error {worst}"
+    if tol is None:
+        tol = TOL if p["fft"] == 32 else TOL_F64_K200
+    assert worst <= tol, f"worst sampled error {worst}"
     return worst
 
 
 def test_tiled_1024_full_size(ctx, oracle_lib):
+    """The benchmark workload: FP64 device path equals the oracle on the whole
+    image; FP32 meets the PSNR gate against the oracle's whole image."""
     job = synth.tiled_1024()[0]
     got, st = run_gpu(ctx, [job])
+    got64, _ = run_gpu(ctx, [job], precision=64, f64=True)
     assert st["tiles"] == 16
+    ref = oracle_run(oracle_lib, job, report=False)
+    lost = job["mask"] > 0
+    assert np.abs(got64[0]["g"][lost] - ref["g"][lost]).max() <= TOL_FP64
+    assert (got64[0]["out"] == ref["out"]).all()
+    err = np.abs(got[0]["out"].astype(int) - ref["out"].astype(int))[lost]
+    dpsnr = psnr(got[0]["out"], job["image"], lost) - psnr(ref["out"], job["image"], lost)
+    assert abs(dpsnr) <= 0.05
+    assert err.max() <= TOL_F64_K200 and (err > 1).mean() < 0.01
     _check_job(oracle_lib, job, got[0], st["lost_blocks"], n_sample=32, seed=1)
 
 
@@ -99,6 +119,8 @@ def test_defects_4k_full_size(ctx, oracle_lib):
     job = synth.defects_4k()[0]
     got, st = run_gpu(ctx, [job])
     _check_job(oracle_lib, job, got[0], st["lost_blocks"], n_sample=48, seed=2)
+    got64, st64 = run_gpu(ctx, [job], precision=64, f64=True)
+    _check_job(oracle_lib, job, got64[0], st64["lost_blocks"], n_sample=24, seed=3, tol=TOL_FP64)
 
 
 def test_batch_subset_16_images(ctx, oracle_lib):
@@ -109,6 +131,9 @@ def test_batch_subset_16_images(ctx, oracle_lib):
     assert st["jobs"] == 16
     for k, (j, g) in enumerate(zip(jobs, got)):
         _check_job(oracle_lib, j, g, None, n_sample=6, seed=10 + k)
+    got64, _ = run_gpu(ctx, jobs, precision=64, f64=True)
+    for k, (j, g) in enumerate(zip(jobs, got64)):
+        _check_job(oracle_lib, j, g, None, n_sample=3, seed=30 + k, tol=TOL_FP64)
 
 
 def test_served_requests(ctx, oracle_lib):
