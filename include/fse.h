@@ -162,6 +162,21 @@ int fse_context_set_option(fse_context_t* ctx, int32_t key, int64_t value);
 int32_t fse_context_kernel_times(fse_context_t* ctx, float* ms, int32_t cap);
 
 /*
+ * fse_autotune -- times the given job mix (device pointers, as for
+ * fse_extrapolate_batch; the outputs are written) under candidate launch
+ * configurations of each work class present: for F = 64 the executor layout
+ * (FSE_OPT_F64_WARPS 4, 2, 8, 5) and the persistent CTAs per SM, for F = 32
+ * the CTAs per SM.  Each candidate runs `reps` times (median of the
+ * iteration-kernel time); the fastest is applied to the context and, when the
+ * context has a tune cache path, written there.  The F = 64 layout is a
+ * process-wide setting.  Writes up to cap results as (class, layout,
+ * ctas_per_sm, milliseconds) quadruples into `trace` (may be NULL) and
+ * returns how many candidates ran, or a negative status.
+ */
+int32_t fse_autotune(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void* cuda_stream,
+                     int32_t reps, double* trace, int32_t cap);
+
+/*
  * fse_extrapolate_batch -- extrapolates n jobs in one stream-ordered pass.
  *   jobs[i].image/mask/out/out_f32 are DEVICE pointers on the context's GPU,
  *   valid until the work on `cuda_stream` (a cudaStream_t; NULL = default

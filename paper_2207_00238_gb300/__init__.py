@@ -67,7 +67,7 @@ EXPORTS = ["fse_plan_tiles", "fse_context_create", "fse_context_destroy", "fse_c
            "fse_extrapolate_batch", "fse_extrapolate_host", "fse_server_create", "fse_submit",
            "fse_poll", "fse_wait", "fse_server_latencies", "fse_server_destroy", "fse_last_error",
            "fse_debug_fetch", "fse_debug_wait_probe", "fse_context_kernel_times",
-           "fse_extrapolate_noalloc"]
+           "fse_extrapolate_noalloc", "fse_autotune"]
 
 _lib = None
 
@@ -101,6 +101,8 @@ def load(path=LIB_PATH):
     L.fse_debug_fetch.restype = i32
     L.fse_debug_wait_probe.argtypes = [vp, i32]
     L.fse_extrapolate_noalloc.argtypes = [P(Job), i32, vp]
+    L.fse_autotune.argtypes = [vp, P(Job), i32, vp, i32, P(ctypes.c_double), i32]
+    L.fse_autotune.restype = i32
     L.fse_context_kernel_times.argtypes = [vp, P(ctypes.c_float), i32]
     L.fse_context_kernel_times.restype = i32
     _lib = L
@@ -213,6 +215,15 @@ class Context:
         K = kmax.value
         useq = useq.ravel()[: cap * K].reshape(cap, K) if K else np.zeros((cap, 0), np.int32)
         return rec[:n], useq[:n]
+
+    def autotune(self, jobs, stream=None, reps=3):
+        """fse_autotune: picks and applies the fastest launch configuration for
+        this job mix; returns the timed candidates (class, layout, ctas, ms)."""
+        arr = (Job * len(jobs))(*jobs)
+        cap = 64
+        tr = (ctypes.c_double * (4 * cap))()
+        n = _check(load().fse_autotune(self.h, arr, len(jobs), stream, reps, tr, cap))
+        return [tuple(tr[4 * i:4 * i + 4]) for i in range(min(n, cap))]
 
     def kernel_times(self, cap=4096):
         """Iteration-kernel milliseconds per call since FSE_OPT_KERNEL_TIMING was set."""

@@ -1,6 +1,7 @@
 // extern "C" entry points declared in include/fse.h.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -16,8 +17,9 @@ using fse::Context;
 
 namespace fse {
 
-// Autotuner cache: one line per work class, "cls ctas_per_sm", keyed by the
-// GPU name on the first line.  A missing or foreign file is ignored.
+// Autotuner cache: the GPU name on the first line, then one line per work
+// class "cls ctas_per_sm layout" (layout: FSE_OPT_F64_WARPS for class 1).
+// A missing or foreign file is ignored.
 void tune_load(Context* c) {
   FILE* f = fopen(c->tune_path.c_str(), "r");
   if (!f) return;
@@ -27,12 +29,116 @@ void tune_load(Context* c) {
   if (fgets(name, sizeof(name), f)) {
     name[strcspn(name, "\r\n")] = 0;
     if (strcmp(name, prop.name) == 0) {
-      int k, v;
-      while (fscanf(f, "%d %d", &k, &v) == 2)
-        if (k >= 0 && k < MAX_CLS && v > 0) c->tuned_ctas[k] = v;
+      int k, v, lay;
+      while (fscanf(f, "%d %d %d", &k, &v, &lay) == 3) {
+        if (k < 0 || k >= MAX_CLS || v <= 0) continue;
+        c->tuned_ctas[k] = v;
+        if (k == CLS_F32_64 && (lay == 2 || lay == 4 || lay == 5 || lay == 8)) set_f64_warps(lay);
+      }
     }
   }
   fclose(f);
+}
+
+static void tune_save(Context* c) {
+  if (c->tune_path.empty()) return;
+  FILE* f = fopen(c->tune_path.c_str(), "w");
+  if (!f) return;
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, c->device);
+  fprintf(f, "%s\n", prop.name);
+  for (int k = 0; k < MAX_CLS; ++k)
+    if (c->tuned_ctas[k] > 0) fprintf(f, "%d %d %d\n", k, c->tuned_ctas[k], k == CLS_F32_64 ? get_f64_warps() : 0);
+  fclose(f);
+}
+
+static int occupancy_of(int cls) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(cls), exec_threads(cls),
+                                                exec_smem(cls));
+  return nb > 0 ? nb : 1;
+}
+
+int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int reps,
+             double* trace, int cap) {
+  if (!c || n <= 0 || !jobs || reps < 1) return fail(FSE_EINVAL, "autotune: bad arguments");
+  bool present[MAX_CLS] = {false, false, false};
+  for (int i = 0; i < n; ++i) {
+    int rc = check_job(jobs[i], i);
+    if (rc) return rc;
+    const fse_params_t& p = jobs[i].p;
+    present[p.precision == 64 ? CLS_F64 : (p.fft == 32 ? CLS_F32_32 : CLS_F32_64)] = true;
+  }
+  const int saved_mode = c->exec_mode, saved_graph = c->use_graph, saved_ctas = c->ctas_per_sm;
+  c->exec_mode = FSE_EXEC_DAG;
+  c->use_graph = 0;
+  int ran = 0;
+  auto time_cfg = [&](int cls, int layout, int ctas, double* ms_out) -> int {
+    c->ctas_per_sm = ctas;
+    std::vector<double> ms;
+    for (int r = 0; r < reps + 1; ++r) {
+      fse_stats_t stt;
+      int rc = run_batch(c, jobs, n, st, &stt, 0);
+      if (rc) return rc;
+      if (r > 0) ms.push_back(stt.exec_ms);  // first run warms up
+    }
+    std::sort(ms.begin(), ms.end());
+    *ms_out = ms[ms.size() / 2];
+    if (trace && ran < cap) {
+      trace[4 * ran] = cls;
+      trace[4 * ran + 1] = layout;
+      trace[4 * ran + 2] = ctas;
+      trace[4 * ran + 3] = *ms_out;
+    }
+    ++ran;
+    return FSE_OK;
+  };
+  int rc = FSE_OK;
+  // F = 64: executor layout x CTAs per SM (only this class is timed; the
+  // others run at their current setting and add a constant)
+  if (present[CLS_F32_64]) {
+    double best = 1e30;
+    int best_lay = get_f64_warps(), best_ctas = 0;
+    const int layouts[4] = {4, 2, 8, 5};
+    for (int li = 0; li < 4 && rc == FSE_OK; ++li) {
+      set_f64_warps(layouts[li]);
+      c->occupancy[CLS_F32_64] = occupancy_of(CLS_F32_64);
+      const int occ = c->occupancy[CLS_F32_64];
+      for (int k = occ; k >= 1 && k >= occ - 1 && rc == FSE_OK; --k) {
+        double ms;
+        rc = time_cfg(CLS_F32_64, layouts[li], k, &ms);
+        if (rc == FSE_OK && ms < best) {
+          best = ms;
+          best_lay = layouts[li];
+          best_ctas = k;
+        }
+      }
+    }
+    set_f64_warps(best_lay);
+    c->occupancy[CLS_F32_64] = occupancy_of(CLS_F32_64);
+    c->tuned_ctas[CLS_F32_64] = best_ctas;
+  }
+  if (present[CLS_F32_32] && rc == FSE_OK) {
+    double best = 1e30;
+    int best_ctas = 0;
+    const int occ = c->occupancy[CLS_F32_32];
+    for (int k = occ; k >= 1 && k >= occ - 3 && rc == FSE_OK; --k) {
+      double ms;
+      rc = time_cfg(CLS_F32_32, 0, k, &ms);
+      if (rc == FSE_OK && ms < best) {
+        best = ms;
+        best_ctas = k;
+      }
+    }
+    c->tuned_ctas[CLS_F32_32] = best_ctas;
+  }
+  c->exec_mode = saved_mode;
+  c->use_graph = saved_graph;
+  c->ctas_per_sm = saved_ctas;
+  c->graph_jobs.clear();
+  if (rc) return rc;
+  tune_save(c);
+  return ran;
 }
 
 // Copies host inputs into the arena front, runs the batch and copies the
@@ -174,6 +280,11 @@ int fse_extrapolate_host(fse_context_t* c, const fse_job_t* jobs, int32_t n, voi
 }
 
 const char* fse_last_error(void) { return fse::last_error(); }
+
+int32_t fse_autotune(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void* cuda_stream,
+                     int32_t reps, double* trace, int32_t cap) {
+  return fse::autotune(ctx, jobs, n, (cudaStream_t)cuda_stream, reps, trace, cap);
+}
 
 int32_t fse_context_kernel_times(fse_context_t* c, float* ms, int32_t cap) {
   if (!c || (!ms && cap > 0)) return fse::fail(FSE_EINVAL, "NULL argument");

@@ -178,6 +178,10 @@ static int context_init(Context** out, int device, size_t arena_bytes, char* ali
   if (tune_path) {
     c->tune_path = tune_path;
     tune_load(c);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(CLS_F32_64),
+                                                  exec_threads(CLS_F32_64), exec_smem(CLS_F32_64));
+    c->occupancy[CLS_F32_64] = std::max(1, nb);
   }
   *out = c;
   return FSE_OK;
@@ -384,7 +388,9 @@ static ExecArgs make_args(Context* c, const Plan& P) {
 }
 
 int exec_grid(Context* c, int k) {
-  int per_sm = c->ctas_per_sm > 0 ? std::min(c->ctas_per_sm, c->occupancy[k]) : c->occupancy[k];
+  int per_sm = c->occupancy[k];
+  if (c->ctas_per_sm > 0) per_sm = std::min(c->ctas_per_sm, c->occupancy[k]);
+  else if (c->tuned_ctas[k] > 0) per_sm = std::min(c->tuned_ctas[k], c->occupancy[k]);
   return std::max(1, per_sm * c->sm_count);
 }
 

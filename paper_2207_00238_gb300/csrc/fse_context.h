@@ -63,5 +63,7 @@ int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse
               size_t arena_offset);
 int exec_grid(Context* c, int cls);
 void tune_load(Context* c);
+int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int reps, double* trace,
+             int cap);
 const char* last_error();
 }  // namespace fse

@@ -220,3 +220,38 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
     job = synth.plain_64()[0]
     got, st = run_gpu(ctx, [job])
     assert st["lost_blocks"] == 26
+
+
+def test_autotune_picks_a_valid_configuration(ctx, oracle_lib, tmp_path):
+    import torch
+    jobs = [_small_tiled(), _defects()]
+    dev = torch.device("cuda", 0)
+    keep, cj, outs = [], [], []
+    for j in jobs:
+        img = torch.from_numpy(j["image"]).to(dev)
+        msk = torch.from_numpy(j["mask"]).to(dev)
+        out = torch.empty_like(img)
+        keep += [img, msk]
+        outs.append(out)
+        cj.append(fse.make_job(img, msk, out, j["params"]))
+    path = str(tmp_path / "tune.txt")
+    c = fse.Context(0, arena_bytes=256 << 20, tune_cache=path)
+    try:
+        trace = c.autotune(cj, reps=2)
+        assert len(trace) >= 3
+        assert {int(t[0]) for t in trace} == {0, 1}
+        got, _ = run_gpu(c, jobs)
+        for j, g in zip(jobs, got):
+            _fp32_check(oracle_lib, j, g)
+        with open(path) as f:
+            lines = f.read().splitlines()
+        assert len(lines) >= 3
+    finally:
+        c.close()
+        ctx.set_option(fse.OPT_F64_WARPS, 0)
+    c2 = fse.Context(0, arena_bytes=256 << 20, tune_cache=path)  # reads the cache back
+    got, _ = run_gpu(c2, jobs)
+    c2.close()
+    ctx.set_option(fse.OPT_F64_WARPS, 0)
+    for j, g in zip(jobs, got):
+        _fp32_check(oracle_lib, j, g)
