@@ -491,6 +491,24 @@ __device__ __forceinline__ uint32_t make_key(float e, uint32_t mask) {
   return k;
 }
 
+// Stores to shared memory only where `pred` holds, as a predicated store
+// (no branch, so the warp never splits around it).
+__device__ __forceinline__ void st_shared_if(bool pred, void* p, float4 v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.v4.f32 [%1], {%2, %3, %4, %5};\n}"
+               ::"r"((unsigned)pred), "r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+__device__ __forceinline__ void st_shared_if(bool pred, void* p, float2 v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.v2.f32 [%1], {%2, %3};\n}"
+               ::"r"((unsigned)pred), "r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_shared_if(bool pred, void* p, int v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.s32 [%1], %2;\n}"
+               ::"r"((unsigned)pred), "r"(a), "r"(v) : "memory");
+}
+
 // Three-input unsigned max.
 __device__ __forceinline__ uint32_t max3u(uint32_t a, uint32_t b, uint32_t c) {
   return max(a, max(b, c));
@@ -608,10 +626,8 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
     const float rux = __shfl_sync(0xffffffffu, v.x, u2);
     const float ruy = __shfl_sync(0xffffffffu, v.y, u2);
     const float dx = gs * rux, dy = gs * ruy;
-    if (lane == 0) {
-      sm.coef_u[iter] = flat;
-      sm.coef_d[iter] = make_float2(dx, dy);
-    }
+    st_shared_if(lane == 0, &sm.coef_u[iter], flat);
+    st_shared_if(lane == 0, &sm.coef_d[iter], make_float2(dx, dy));
     if (iter + 1 == K) break;
     const float2* wp = sm.Wd + (32 - u1) * 32 + ((lane - u2) & 31);
     const float ndx = -dx, ndy = -dy;
@@ -832,11 +848,9 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
       const int i_w = RPT - 1 - (int)(wbest & (uint32_t)(RPT - 1));
       const int tw = (warp << 5) | l_w;  // the winning thread
       const int flat_w = (i_w + RPT * (tw >> 6)) * 64 + (tw & 63);
-      float2 v = select_reg<RPT>(R, i_w);
-      v.x = __shfl_sync(0xffffffffu, v.x, l_w);
-      v.y = __shfl_sync(0xffffffffu, v.y, l_w);
-      if (lane == 0)
-        sm.xrec[iter & 1][warp] = make_float4(__uint_as_float(wbest), __int_as_float(flat_w), v.x, v.y);
+      const float2 v = select_reg<RPT>(R, i_w);  // meaningful in lane l_w only
+      st_shared_if(lane == l_w, &sm.xrec[iter & 1][warp],
+                   make_float4(__uint_as_float(wbest), __int_as_float(flat_w), v.x, v.y));
     }
     __syncthreads();
     // largest key over the warps (lowest flat index on equal keys), carrying R_u
@@ -851,10 +865,8 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     const int u1 = flat >> 6, u2 = flat & 63;
     const float2 ru = make_float2(rb.z, rb.w);
     const float dx = gs * ru.x, dy = gs * ru.y;
-    if (t == 0) {
-      sm.coef_u[iter] = flat;
-      sm.coef_d[iter] = make_float2(dx, dy);
-    }
+    st_shared_if(t == 0, &sm.coef_u[iter], flat);
+    st_shared_if(t == 0, &sm.coef_d[iter], make_float2(dx, dy));
     if (iter + 1 == K) break;
     const int r0 = RPT * q - u1;  // first W row of this thread, mod 64
     const float2* wp =
