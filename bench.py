@@ -66,6 +66,8 @@ def parse():
                     help="measured requests of the serving leg (0 = skip)")
     ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 8])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--order", default=None, choices=[None, "phased", "raster", "independent"],
+                    help="processing order override (default: the workload's, PHASED)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     return ap.parse_args()
 
@@ -295,6 +297,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     fse.build()
     jobs = workload(args.workload)
+    if args.order:
+        for j in jobs:
+            j["params"] = dict(j["params"], order=args.order)
     dev = torch.device("cuda", local)
     ctx = fse.Context(local, arena_bytes=args.arena_mb << 20)
     ctx.exec_mode(args.mode)

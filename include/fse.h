@@ -95,7 +95,20 @@ typedef struct fse_params_t {
     int32_t n_tiles;   /* N of Algorithm 1 (>= 1)                            */
     int32_t overlap;   /* d (>= 0)                                           */
     int32_t precision; /* 32: FP32 fast path; 64: FP64 validation path       */
+    int32_t tiling;    /* FSE_TILING_ALG1 (0) or FSE_TILING_VERTICAL (1)      */
 } fse_params_t;
+
+/* Tilings.  ALG1: Algorithm 1 (Eqs. 1-5).  VERTICAL: the baseline the paper
+ * compares against (Sec. III): N full-height stripes, widths distributed as in
+ * Eq. 5 (the first W mod N stripes one pixel wider); it needs no landscape
+ * swap.  Both are extended by the overlap stripe d. */
+#define FSE_TILING_ALG1 0
+#define FSE_TILING_VERTICAL 1
+
+/* fse_plan_tiles_vertical -- the VERTICAL tiling with overlap d; arguments,
+ * output layout and errors as for fse_plan_tiles. */
+int fse_plan_tiles_vertical(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out,
+                            int32_t cap, int32_t* n_out);
 
 typedef struct fse_job_t {
     const uint8_t* image; /* W x H, row pitch `pitch` bytes                   */

@@ -60,7 +60,8 @@ def lib():
         _lib.oracle_fse_image.argtypes = [P(ctypes.c_uint8), P(ctypes.c_uint8), i32, i32, i32, i32,
                                           i32, i32, f64, f64, f64, i32, i32, i32, f64,
                                           P(ctypes.c_uint8), P(f64), P(_BlkReport), P(i32), i32,
-                                          P(i32), i32, i32, ctypes.c_int64, P(ctypes.c_int64)]
+                                          P(i32), i32, i32, ctypes.c_int64, P(ctypes.c_int64), i32]
+        _lib.oracle_plan_vertical.argtypes = [i32, i32, i32, i32, P(i32), i32, P(i32)]
         _lib.oracle_threads.restype = ctypes.c_int
         _lib.oracle_fse_block_alone.restype = f64
         _lib.oracle_fse_block_alone.argtypes = [P(ctypes.c_uint8), P(ctypes.c_uint8)] + [i32] * 10 + \
@@ -76,12 +77,13 @@ def threads():
     return lib().oracle_threads()
 
 
-def plan_tiles(W, H, N, d):
-    """Algorithm 1 + overlap stripe d.  Returns (rc, int32 array [n, 8]):
-    columns x, y, w, h, ex, ey, ew, eh."""
+def plan_tiles(W, H, N, d, tiling="alg1"):
+    """Algorithm 1 (or the vertical stripes) + overlap stripe d.  Returns
+    (rc, int32 array [n, 8]): columns x, y, w, h, ex, ey, ew, eh."""
     out = np.zeros((max(N, 1), 8), np.int32)
     n = ctypes.c_int32(0)
-    rc = lib().oracle_plan_tiles(W, H, N, d, _ptr(out, ctypes.c_int32), max(N, 1), ctypes.byref(n))
+    fn = lib().oracle_plan_vertical if tiling == "vertical" else lib().oracle_plan_tiles
+    rc = fn(W, H, N, d, _ptr(out, ctypes.c_int32), max(N, 1), ctypes.byref(n))
     return rc, out[: n.value]
 
 
@@ -133,7 +135,7 @@ def fse_block_alone(img, mask, tile, I, J, *, block, border, fft, K, rho=0.8, ga
 
 def fse_image(img, mask, *, block, border, fft, K, rho=0.8, delta=0.5, gamma=0.5,
               order="phased", n_tiles=1, overlap=32, tau=1e-9, report=False, threads=0,
-              literal_seq=False, max_blocks=0):
+              literal_seq=False, max_blocks=0, tiling="alg1"):
     """Whole-image FSE on the overlapping tiles of Algorithm 1.
     Returns dict(rc, out (u8), g (f64, NaN at known pixels), stats, blocks, useq)."""
     img = np.ascontiguousarray(img, np.uint8)
@@ -146,7 +148,7 @@ def fse_image(img, mask, *, block, border, fft, K, rho=0.8, delta=0.5, gamma=0.5
     rep = useq = None
     if report:
         nbmax = sum(((int(t[6]) + block - 1) // block) * ((int(t[7]) + block - 1) // block)
-                    for t in plan_tiles(W, H, n_tiles, overlap)[1])
+                    for t in plan_tiles(W, H, n_tiles, overlap, tiling)[1])
         cap = max(nbmax, 1)
         rep = (_BlkReport * cap)()
         useq = np.zeros((cap, max(K, 1)), np.int32)
@@ -155,7 +157,8 @@ def fse_image(img, mask, *, block, border, fft, K, rho=0.8, delta=0.5, gamma=0.5
         _ptr(img, ctypes.c_uint8), _ptr(mask, ctypes.c_uint8), W, H, block, border, fft, K, rho,
         delta, gamma, ORDER[order], n_tiles, overlap, tau, _ptr(out, ctypes.c_uint8),
         _ptr(g, ctypes.c_double), rep, _ptr(useq, ctypes.c_int32), cap, ctypes.byref(nrep),
-        threads, int(literal_seq), max_blocks, _ptr(stats, ctypes.c_int64))
+        threads, int(literal_seq), max_blocks, _ptr(stats, ctypes.c_int64),
+        1 if tiling == "vertical" else 0)
     res = dict(rc=rc, out=out, g=g, stats=dict(processed=int(stats[0]), empty=int(stats[1]),
                                                tiles=int(stats[2]), core_lost=int(stats[3])))
     if report:

@@ -125,6 +125,26 @@ int oracle_plan_tiles(int32_t W32, int32_t H32, int32_t N32, int32_t d32,
     return OR_OK;
 }
 
+/* The comparison tiling of Sec. III: N vertical stripes of full height,
+ * widths floor(W/N) with the first W mod N one wider (the Eq. 5 rule). */
+int oracle_plan_vertical(int32_t W, int32_t H, int32_t N, int32_t d, int32_t *out, int32_t cap,
+                         int32_t *n_out) {
+    if (n_out) *n_out = 0;
+    if (W <= 0 || H <= 0 || N <= 0 || d < 0 || cap < N) return OR_EINVAL;
+    int64_t x = 0;
+    for (int j = 1; j <= N; j++) {
+        int64_t w = W / N + (j <= W % N ? 1 : 0);
+        if (w <= 0) return OR_EDEGENERATE;
+        int64_t x0 = x - d < 0 ? 0 : x - d, x1 = x + w + d > W ? W : x + w + d;
+        int32_t *o = out + 8 * (j - 1);
+        o[0] = (int32_t)x; o[1] = 0; o[2] = (int32_t)w; o[3] = H;
+        o[4] = (int32_t)x0; o[5] = 0; o[6] = (int32_t)(x1 - x0); o[7] = H;
+        x += w;
+    }
+    if (n_out) *n_out = N;
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* 2. FSE on one block's support (Sec. II): greedy weighted model fit.      */
 /* ------------------------------------------------------------------------ */
@@ -280,7 +300,7 @@ int oracle_fse_image(const uint8_t *img, const uint8_t *mask, int32_t W, int32_t
                      double gamma, int32_t order, int32_t N, int32_t d, double tau,
                      uint8_t *out, double *out_g, blk_report_t *rep, int32_t *useq,
                      int32_t rep_cap, int32_t *n_rep, int32_t nthreads, int32_t literal_seq,
-                     int64_t max_blocks, int64_t *stats) {
+                     int64_t max_blocks, int64_t *stats, int32_t tiling) {
     if (n_rep) *n_rep = 0;
     if (b <= 0 || B < 0 || K < 0 || F <= 0) return OR_EINVAL;
     const int S = b + 2 * B;
@@ -289,7 +309,8 @@ int oracle_fse_image(const uint8_t *img, const uint8_t *mask, int32_t W, int32_t
     if (order < 0 || order > 2) return OR_EINVAL;
     int32_t *tiles = malloc(sizeof(int32_t) * 8 * (size_t)(N > 0 ? N : 1));
     int32_t nt = 0;
-    int rc = oracle_plan_tiles(W, H, N, d, tiles, N, &nt);
+    int rc = tiling == 1 ? oracle_plan_vertical(W, H, N, d, tiles, N, &nt)
+                         : oracle_plan_tiles(W, H, N, d, tiles, N, &nt);
     if (rc != OR_OK) { free(tiles); return rc; }
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);

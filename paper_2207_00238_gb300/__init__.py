@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfse.so")
 
 OK, EINVAL, EDEGENERATE, ENOMEM, EBUSY, ETIMEOUT, ECUDA, ENOTFOUND, ECANCELLED = 0, -1, -2, -3, -4, -5, -6, -7, -8
 ORDER = {"phased": 0, "raster": 1, "independent": 2}
+TILING = {"alg1": 0, "vertical": 1}
 OPT_EXEC_MODE, OPT_TIMEOUT_MS, OPT_CTAS_PER_SM, OPT_USE_GRAPH, OPT_DEBUG_CAPTURE, OPT_KERNEL_TIMING, OPT_F64_WARPS = 1, 2, 3, 4, 5, 6, 7
 EXEC = {"dag": 0, "levels": 1, "per_block": 2}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -37,7 +38,8 @@ class Params(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("border", ctypes.c_int32), ("fft", ctypes.c_int32),
                 ("K", ctypes.c_int32), ("rho", ctypes.c_double), ("delta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("order", ctypes.c_int32), ("n_tiles", ctypes.c_int32),
-                ("overlap", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("overlap", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tiling", ctypes.c_int32)]
 
 
 class Job(ctypes.Structure):
@@ -63,7 +65,7 @@ class ServerCfg(ctypes.Structure):
                 ("max_resident", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
 
 
-EXPORTS = ["fse_plan_tiles", "fse_context_create", "fse_context_destroy", "fse_context_set_option",
+EXPORTS = ["fse_plan_tiles", "fse_plan_tiles_vertical", "fse_context_create", "fse_context_destroy", "fse_context_set_option",
            "fse_extrapolate_batch", "fse_extrapolate_host", "fse_server_create", "fse_submit",
            "fse_poll", "fse_wait", "fse_server_latencies", "fse_server_destroy", "fse_last_error",
            "fse_debug_fetch", "fse_debug_wait_probe", "fse_context_kernel_times",
@@ -82,6 +84,7 @@ def load(path=LIB_PATH):
     L = ctypes.CDLL(path)
     P, i32, vp = ctypes.POINTER, ctypes.c_int32, ctypes.c_void_p
     L.fse_plan_tiles.argtypes = [i32, i32, i32, i32, P(Tile), i32, P(i32)]
+    L.fse_plan_tiles_vertical.argtypes = [i32, i32, i32, i32, P(Tile), i32, P(i32)]
     L.fse_context_create.argtypes = [P(vp), ctypes.c_int, ctypes.c_size_t, ctypes.c_char_p]
     L.fse_context_destroy.argtypes = [vp]
     L.fse_context_destroy.restype = None
@@ -119,12 +122,14 @@ def _check(rc):
     return rc
 
 
-def plan_tiles(W, H, N, d):
-    """Algorithm 1 + overlap d.  Returns int32 array [N, 8] (x, y, w, h, ex, ey, ew, eh)."""
+def plan_tiles(W, H, N, d, tiling="alg1"):
+    """Algorithm 1 (or the vertical stripes) + overlap d.  Returns int32 array
+    [N, 8] (x, y, w, h, ex, ey, ew, eh)."""
     L = load()
     arr = (Tile * max(N, 1))()
     n = ctypes.c_int32(0)
-    _check(L.fse_plan_tiles(W, H, N, d, arr, max(N, 1), ctypes.byref(n)))
+    fn = L.fse_plan_tiles_vertical if tiling == "vertical" else L.fse_plan_tiles
+    _check(fn(W, H, N, d, arr, max(N, 1), ctypes.byref(n)))
     return np.array([[getattr(arr[i], f) for f, _ in Tile._fields_] for i in range(n.value)],
                     np.int32).reshape(-1, 8)
 
@@ -138,9 +143,10 @@ def extrapolate_noalloc(jobs, stream=None):
 
 
 def make_params(block, border, fft, K, rho=0.8, delta=0.5, gamma=0.5, order="phased",
-                n_tiles=1, overlap=32, precision=32, **_):
+                n_tiles=1, overlap=32, precision=32, tiling="alg1", **_):
     return Params(block, border, fft, K, rho, delta, gamma,
-                  ORDER[order] if isinstance(order, str) else int(order), n_tiles, overlap, precision)
+                  ORDER[order] if isinstance(order, str) else int(order), n_tiles, overlap, precision,
+                  TILING[tiling] if isinstance(tiling, str) else int(tiling))
 
 
 def _ptr(t):

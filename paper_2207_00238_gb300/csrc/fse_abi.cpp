@@ -214,6 +214,11 @@ int fse_plan_tiles(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out, 
   return fse::plan_tiles(W, H, N, d, out, cap, n_out);
 }
 
+int fse_plan_tiles_vertical(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out,
+                            int32_t cap, int32_t* n_out) {
+  return fse::plan_tiles_vertical(W, H, N, d, out, cap, n_out);
+}
+
 int fse_context_create(fse_context_t** ctx, int device, size_t arena_bytes,
                        const char* tune_cache_path) {
   if (!ctx) return fse::fail(FSE_EINVAL, "NULL ctx");

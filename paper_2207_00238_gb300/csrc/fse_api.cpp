@@ -94,6 +94,31 @@ int plan_tiles(int32_t W0, int32_t H0, int32_t N, int32_t d, fse_tile_t* out, in
   return FSE_OK;
 }
 
+// Vertical stripes (the paper's comparison tiling): N full-height tiles,
+// widths W/N with the first W mod N one pixel wider.
+int plan_tiles_vertical(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out, int32_t cap,
+                        int32_t* n_out) {
+  if (n_out) *n_out = 0;
+  if (W <= 0 || H <= 0 || N <= 0 || d < 0 || out == nullptr || cap < N)
+    return fail(FSE_EINVAL, "fse_plan_tiles_vertical: invalid arguments");
+  int64_t x = 0;
+  for (int32_t j = 1; j <= N; ++j) {
+    const int64_t w = W / N + (j <= W % N ? 1 : 0);
+    if (w <= 0) return fail(FSE_EDEGENERATE, "fse_plan_tiles_vertical: %d stripes for width %d", N, W);
+    const int64_t x0 = std::max<int64_t>(0, x - d), x1 = std::min<int64_t>(W, x + w + d);
+    out[j - 1] = {(int32_t)x, 0, (int32_t)w, H, (int32_t)x0, 0, (int32_t)(x1 - x0), H};
+    x += w;
+  }
+  if (n_out) *n_out = N;
+  return FSE_OK;
+}
+
+int plan_tiles_mode(int32_t mode, int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out,
+                    int32_t cap, int32_t* n_out) {
+  return mode == FSE_TILING_VERTICAL ? plan_tiles_vertical(W, H, N, d, out, cap, n_out)
+                                     : plan_tiles(W, H, N, d, out, cap, n_out);
+}
+
 // ---------------------------------------------------------------------------
 // parameter checks
 // ---------------------------------------------------------------------------
@@ -115,6 +140,8 @@ int check_job(const fse_job_t& j, int idx) {
   if (p.n_tiles < 1 || p.overlap < 0) return fail(FSE_EINVAL, "job %d: n_tiles/overlap", idx);
   if (p.precision != 32 && p.precision != 64)
     return fail(FSE_EINVAL, "job %d: precision %d must be 32 or 64", idx, p.precision);
+  if (p.tiling != FSE_TILING_ALG1 && p.tiling != FSE_TILING_VERTICAL)
+    return fail(FSE_EINVAL, "job %d: tiling %d", idx, p.tiling);
   if ((j.W + p.block - 1) / p.block >= 32768 || (j.H + p.block - 1) / p.block >= 32768)
     return fail(FSE_EINVAL, "job %d: image too large for block %d", idx, p.block);
   return FSE_OK;
@@ -257,7 +284,7 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
     const fse_params_t& p = j.p;
     tl.resize(p.n_tiles);
     int32_t nt = 0;
-    rc = plan_tiles(j.W, j.H, p.n_tiles, p.overlap, tl.data(), p.n_tiles, &nt);
+    rc = plan_tiles_mode(p.tiling, j.W, j.H, p.n_tiles, p.overlap, tl.data(), p.n_tiles, &nt);
     if (rc) return rc;
     JobDev& J = P.jobs[i];
     J.image = j.image;

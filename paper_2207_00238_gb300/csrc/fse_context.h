@@ -52,6 +52,10 @@ int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 int plan_tiles(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out, int32_t cap,
                int32_t* n_out);
+int plan_tiles_mode(int32_t mode, int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out,
+                    int32_t cap, int32_t* n_out);
+int plan_tiles_vertical(int32_t W, int32_t H, int32_t N, int32_t d, fse_tile_t* out, int32_t cap,
+                        int32_t* n_out);
 int check_job(const fse_job_t& j, int idx);
 int context_create(Context** out, int device, size_t arena_bytes, const char* tune_path);
 // A context on caller-owned device memory (not freed by context_destroy).

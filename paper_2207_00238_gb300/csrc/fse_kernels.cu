@@ -164,7 +164,7 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
     delta = J.delta;
   }
   const bool use_done = J.order != ORDER_INDEPENDENT;
-  constexpr int U = 4;  // pixels per thread whose loads are in flight together
+  constexpr int U = 8;  // pixels per thread whose loads are in flight together
   for (int e0 = t; e0 < S * S; e0 += U * nthr) {
     uint8_t mk[U], px[U];
     real wi[U], v[U];

@@ -107,7 +107,7 @@ int run(const fse_job_t* jobs, int32_t n, cudaStream_t st) {
     if (nt + p.n_tiles > kMaxTiles)
       return fail(FSE_EINVAL, "noalloc: more than %d tiles in one call", kMaxTiles);
     int32_t got = 0;
-    rc = plan_tiles(j.W, j.H, p.n_tiles, p.overlap, g_tl + nt, p.n_tiles, &got);
+    rc = plan_tiles_mode(p.tiling, j.W, j.H, p.n_tiles, p.overlap, g_tl + nt, p.n_tiles, &got);
     if (rc) return rc;
     JobDev& J = g_jobs[i];
     memset(&J, 0, sizeof(J));

@@ -253,7 +253,8 @@ int fse_submit(fse_server_t* s, const fse_job_t* job, uint64_t* ticket) {
   if (rc) return rc;
   int32_t nt = 0;
   std::vector<fse_tile_t> tl(job->p.n_tiles);
-  rc = fse::plan_tiles(job->W, job->H, job->p.n_tiles, job->p.overlap, tl.data(), job->p.n_tiles, &nt);
+  rc = fse::plan_tiles_mode(job->p.tiling, job->W, job->H, job->p.n_tiles, job->p.overlap, tl.data(),
+                            job->p.n_tiles, &nt);
   if (rc) return rc;
   auto r = std::make_shared<Request>();
   r->job = *job;

@@ -38,4 +38,4 @@ def oracle_run(oracle, job, report=True, **over):
     return oracle.fse_image(job["image"], job["mask"], block=p["block"], border=p["border"],
                             fft=p["fft"], K=p["K"], rho=p["rho"], delta=p["delta"],
                             gamma=p["gamma"], order=p["order"], n_tiles=p["n_tiles"],
-                            overlap=p["overlap"], report=report)
+                            overlap=p["overlap"], report=report, tiling=p.get("tiling", "alg1"))

@@ -255,3 +255,12 @@ def test_autotune_picks_a_valid_configuration(ctx, oracle_lib, tmp_path):
     ctx.set_option(fse.OPT_F64_WARPS, 0)
     for j, g in zip(jobs, got):
         _fp32_check(oracle_lib, j, g)
+
+
+def test_vertical_tiling_fp64_sequence_and_fp32(ctx, oracle_lib):
+    job = _small_tiled(W=128, H=64, K=40, n_tiles=3)
+    job["params"] = dict(job["params"], tiling="vertical", overlap=12)
+    _seq_check(oracle_lib, ctx, job)
+    got, st = run_gpu(ctx, [job])
+    assert st["tiles"] == 3
+    _fp32_check(oracle_lib, job, got[0])

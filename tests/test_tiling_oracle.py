@@ -86,3 +86,23 @@ def test_compact_equal_area(oracle_lib):
         a = t[:, 2] * t[:, 3]
         assert a.max() / a.min() < 1.1
         assert (np.maximum(t[:, 2], t[:, 3]) / np.minimum(t[:, 2], t[:, 3])).max() < 2.0
+
+
+def test_vertical_stripes_hand_golden(oracle_lib):
+    # 1024 = 22 * 46 + 12: the first 12 stripes are 47 wide, the other 10 are 46
+    rc, t = oracle_lib.plan_tiles(1024, 480, 22, 0, "vertical")
+    assert rc == 0
+    assert t[:, 2].tolist() == [47] * 12 + [46] * 10
+    assert (t[:, 1] == 0).all() and (t[:, 3] == 480).all()
+    assert t[:, 0].tolist() == list(np.cumsum([0] + [47] * 12 + [46] * 9))
+
+
+def test_vertical_overlap_exceeds_alg1(oracle_lib):
+    """Sec. III: stripes have the longer boundary, so their overlap stripes
+    add more processed pixels than the compact tiles of Algorithm 1."""
+    for W, H, N, d in [(6024, 4024, 32, 32), (1024, 480, 22, 32), (3840, 2160, 16, 32)]:
+        areas = {}
+        for tiling in ["alg1", "vertical"]:
+            _, t = oracle_lib.plan_tiles(W, H, N, d, tiling)
+            areas[tiling] = int((t[:, 6] * t[:, 7]).sum())
+        assert areas["vertical"] > areas["alg1"] > W * H
