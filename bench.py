@@ -66,6 +66,8 @@ def parse():
                     help="measured requests of the serving leg (0 = skip)")
     ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 8])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--study", default=None, choices=[None, "overlap", "tiling"],
+                    help="run a study instead of the benchmark (one JSON line per result)")
     ap.add_argument("--order", default=None, choices=[None, "phased", "raster", "independent"],
                     help="processing order override (default: the workload's, PHASED)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -277,6 +279,81 @@ def serve_leg(fse, device, n_measured, n_warm=100, pool_size=16, rate_hz=200.0):
 
 
 # ---------------------------------------------------------------------------
+# studies (not part of the default run)
+# ---------------------------------------------------------------------------
+def paper_scale_jobs(loss):
+    """6024x4024 stand-in for the paper's test images (Sec. IV) with `loss` of
+    the 4x4 blocks lost (bursts and isolated), b=4, B=14, F=32, K=100."""
+    from paper_2207_00238_gb300 import synth
+    W, H = 6024, 4024
+    rng = synth.Rng(synth.SEED_BASE + 60)
+    img = synth.image(W, H, rng, structure=True)
+    nb = ((W + 3) // 4) * ((H + 3) // 4)
+    mask, _ = synth.block_mask(W, H, 4, int(round(loss * nb)), synth.Rng(synth.SEED_BASE + 61))
+    return img, mask
+
+
+def run_study(args):
+    import torch
+    import paper_2207_00238_gb300 as fse
+    from paper_2207_00238_gb300 import synth
+    fse.build()
+    dev = torch.device("cuda", 0)
+    ctx = fse.Context(0, arena_bytes=16 << 30)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def run(img_d, msk_d, out_d, p, reps=2):
+        job = fse.make_job(img_d, msk_d, out_d, p)
+        st = None
+        for _ in range(reps):
+            st = ctx.extrapolate([job], stream=stream, stats=True)
+        return st
+
+    def psnr_all(out, img):
+        d = out.astype(np.float64) - img.astype(np.float64)
+        return 10 * np.log10(255.0 ** 2 / np.mean(d * d))
+
+    if args.study == "overlap":
+        for loss in (0.14, 0.62):
+            img, mask = paper_scale_jobs(loss)
+            img_d = torch.from_numpy(img).to(dev)
+            msk_d = torch.from_numpy(mask).to(dev)
+            out_d = torch.empty_like(img_d)
+            base = synth.params(4, 14, 32, 100)
+            st = run(img_d, msk_d, out_d, dict(base, n_tiles=1, overlap=0))
+            ref = psnr_all(out_d.cpu().numpy(), img)
+            print(json.dumps({"study": "overlap", "loss": loss, "n_tiles": 1, "overlap": 0,
+                              "psnr_db": ref, "lost_blocks": st["lost_blocks"],
+                              "exec_ms": st["exec_ms"]}), flush=True)
+            for d in (0, 1, 2, 4, 8, 16, 24, 32, 48, 64, 96):
+                st = run(img_d, msk_d, out_d, dict(base, n_tiles=32, overlap=d))
+                ps = psnr_all(out_d.cpu().numpy(), img)
+                print(json.dumps({"study": "overlap", "loss": loss, "n_tiles": 32, "overlap": d,
+                                  "psnr_db": ps, "delta_vs_untiled_db": ps - ref,
+                                  "lost_blocks": st["lost_blocks"], "exec_ms": st["exec_ms"]}),
+                      flush=True)
+    else:
+        for W, H in ((1024, 480), (6024, 4024)):
+            for N in (2, 4, 8, 16, 22, 32, 64):
+                row = {"study": "tiling", "W": W, "H": H, "n_tiles": N, "overlap": 32}
+                for tiling in ("alg1", "vertical"):
+                    t = fse.plan_tiles(W, H, N, 32, tiling)
+                    row[f"processed_over_image_{tiling}"] = float((t[:, 6] * t[:, 7]).sum()) / (W * H)
+                print(json.dumps(row), flush=True)
+        img, mask = paper_scale_jobs(0.62)
+        img_d = torch.from_numpy(img).to(dev)
+        msk_d = torch.from_numpy(mask).to(dev)
+        out_d = torch.empty_like(img_d)
+        for tiling in ("alg1", "vertical"):
+            st = run(img_d, msk_d, out_d, synth.params(4, 14, 32, 100, n_tiles=32, overlap=32,
+                                                       tiling=tiling), reps=3)
+            print(json.dumps({"study": "tiling_gpu", "tiling": tiling, "n_tiles": 32, "overlap": 32,
+                              "loss": 0.62, "lost_blocks": st["lost_blocks"],
+                              "exec_ms": st["exec_ms"], "device_ms": st["device_ms"]}), flush=True)
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -286,6 +363,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.study:
+        return run_study(args)
 
     import torch
     import paper_2207_00238_gb300 as fse
