@@ -712,7 +712,7 @@ struct alignas(16) CtaSmem64 {
 
 template <int NWB, int ROWS>
 __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
-  constexpr int NT = NWB * 32, RPT = 4096 / NT, NQ = NT / 64;
+  constexpr int NT = NWB * 32, RPT = 4096 / NT;
   const ClassArgs& C = a.c[CLS_F32_64];
   const int2 it = C.items[id];
   copy_desc(&sm.T, a.tiles + it.x, t, NT);
