@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--arena-mb", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="measured requests of the serving leg (0 = skip)")
-    ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 8])
+    ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 6, 8])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--study", default=None, choices=[None, "overlap", "tiling"],
                     help="run a study instead of the benchmark (one JSON line per result)")

@@ -156,7 +156,9 @@ void fse_context_destroy(fse_context_t* ctx);
 #define FSE_OPT_F64_WARPS 7     /* layout of the F = 64 FP32 executor: warps per
                                    block 2 (64 bins per thread), 4 (32) or 8 (16);
                                    5 = 4 warps with a 96-row W table (4 blocks
-                                   per SM); 0 = default                        */
+                                   per SM); 6 = 4 warps, bins paired for the
+                                   two-wide FP32 instructions (W table of
+                                   16-byte slots, 67 KB); 0 = default (6)      */
 #define FSE_OPT_KERNEL_TIMING 6 /* 1 = bracket the iteration kernels of every
                                    call with CUDA events (no synchronisation);
                                    read with fse_context_kernel_times         */
@@ -178,7 +180,7 @@ int32_t fse_context_kernel_times(fse_context_t* ctx, float* ms, int32_t cap);
  * fse_autotune -- times the given job mix (device pointers, as for
  * fse_extrapolate_batch; the outputs are written) under candidate launch
  * configurations of each work class present: for F = 64 the executor layout
- * (FSE_OPT_F64_WARPS 4, 2, 8, 5) and the persistent CTAs per SM, for F = 32
+ * (FSE_OPT_F64_WARPS 6, 4, 5, 2, 8) and the persistent CTAs per SM, for F = 32
  * the CTAs per SM.  Each candidate runs `reps` times (median of the
  * iteration-kernel time); the fastest is applied to the context and, when the
  * context has a tune cache path, written there.  The F = 64 layout is a

@@ -33,7 +33,7 @@ void tune_load(Context* c) {
       while (fscanf(f, "%d %d %d", &k, &v, &lay) == 3) {
         if (k < 0 || k >= MAX_CLS || v <= 0) continue;
         c->tuned_ctas[k] = v;
-        if (k == CLS_F32_64 && (lay == 2 || lay == 4 || lay == 5 || lay == 8)) set_f64_warps(lay);
+        if (k == CLS_F32_64 && (lay == 2 || lay == 4 || lay == 5 || lay == 6 || lay == 8)) set_f64_warps(lay);
       }
     }
   }
@@ -99,8 +99,8 @@ int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int 
   if (present[CLS_F32_64]) {
     double best = 1e30;
     int best_lay = get_f64_warps(), best_ctas = 0;
-    const int layouts[4] = {4, 2, 8, 5};
-    for (int li = 0; li < 4 && rc == FSE_OK; ++li) {
+    const int layouts[5] = {6, 4, 5, 2, 8};
+    for (int li = 0; li < 5 && rc == FSE_OK; ++li) {
       set_f64_warps(layouts[li]);
       c->occupancy[CLS_F32_64] = occupancy_of(CLS_F32_64);
       const int occ = c->occupancy[CLS_F32_64];
@@ -249,9 +249,9 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       c->debug = value != 0;
       return FSE_OK;
     case FSE_OPT_F64_WARPS: {
-      if (value != 0 && value != 2 && value != 4 && value != 5 && value != 8)
+      if (value != 0 && value != 2 && value != 4 && value != 5 && value != 6 && value != 8)
         return fse::fail(FSE_EINVAL, "f64 warps");
-      fse::set_f64_warps(value == 0 ? 4 : (int)value);
+      fse::set_f64_warps(value == 0 ? 6 : (int)value);
       int nb = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fse::exec_kernel_ptr(fse::CLS_F32_64),
                                                     fse::exec_threads(fse::CLS_F32_64),

@@ -710,9 +710,11 @@ struct alignas(16) CtaSmem64 {
   JobDev J;
 };
 
-template <int NWB, int ROWS>
-__device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
-  constexpr int NT = NWB * 32, RPT = 4096 / NT;
+// Prologue of one F = 64 block: descriptors into shared memory, the support
+// staged into zbuf (64 x 64, swizzled) and transformed in place by the 2-D FFT.
+// Ends behind a barrier.
+template <int NT, class Sm>
+__device__ __forceinline__ void stage_fft64(const ExecArgs& a, int id, Sm& sm, float2* zbuf, int t) {
   const ClassArgs& C = a.c[CLS_F32_64];
   const int2 it = C.items[id];
   copy_desc(&sm.T, a.tiles + it.x, t, NT);
@@ -722,10 +724,9 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
-  const int S = J.S, K = J.K;
+  const int S = J.S;
   float* val = a.val_f + T.val_off;
   if (t == 0) debug_record(a, CLS_F32_64, id, T, it.x, I, Jb);
-  float2* zbuf = ROWS == 128 ? sm.Wd + 64 * 64 : sm.Wd;
 
   stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, NT);
   __syncthreads();
@@ -767,6 +768,20 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     }
   }
   __syncthreads();
+}
+
+template <int NWB, int ROWS>
+__device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
+  constexpr int NT = NWB * 32, RPT = 4096 / NT;
+  const ClassArgs& C = a.c[CLS_F32_64];
+  float2* zbuf = ROWS == 128 ? sm.Wd + 64 * 64 : sm.Wd;
+  stage_fft64<NT>(a, id, sm, zbuf, t);
+  const int2 it = C.items[id];
+  const TileDev& T = sm.T;
+  const JobDev& J = sm.J;
+  const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+  const int K = J.K;
+  float* val = a.val_f + T.val_off;
   const int c = t & 63, q = t >> 6, lane = t & 31, warp = t >> 5;
   float2 R[RPT];
   if constexpr (ROWS == 128) {
@@ -898,6 +913,163 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
                                       NT);
 }
 
+// ---------------------------------------------------------------------------
+// Paired-bin layout of the F = 64 executor (ROWS = ROWS_PAIRED, 4 warps).
+// Thread t = 32 g + p owns the bins (k1, p) and (k1, p + 32) for the 16 rows
+// k1 = 16 m + 4 g + j (m, j = 0..3), held as pairs: RX[4m + j] = (Re R(k1, p),
+// Re R(k1, p + 32)), RY likewise for Im.  W is a table of 16-byte slots,
+// slot (r, d) = (Re W(r, d), Re W(r, d ^ 32), Im W(r, d), Im W(r, d ^ 32)), so
+// one 16-byte load gives W(k - u) for both bins of a pair, split into real and
+// imaginary pairs: the update and the energy of two bins are six paired FP32
+// instructions (fma.rn.f32x2 / mul.rn.f32x2) that round exactly like the
+// scalar forms.  Each thread reads its rows in four runs of four; the table
+// repeats rows 0..2 as rows 64..66 so a run that wraps stays contiguous.
+// ---------------------------------------------------------------------------
+constexpr int ROWS_PAIRED = 134;  // 67 rows of 64 float4 slots, counted in float2 rows
+
+__device__ __forceinline__ float4 swap_pair(float4 v) { return make_float4(v.y, v.x, v.w, v.z); }
+
+template <int NWB, int ROWS>
+__device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
+  static_assert(NWB == 4 && ROWS == ROWS_PAIRED, "paired layout: 4 warps, 67 table rows");
+  constexpr int NT = 128;
+  const ClassArgs& C = a.c[CLS_F32_64];
+  float2* zbuf = sm.Wd;  // the FFT buffer is table rows 0..31
+  float4* Wt = reinterpret_cast<float4*>(sm.Wd);
+  stage_fft64<NT>(a, id, sm, zbuf, t);
+  const int2 it = C.items[id];
+  const TileDev& T = sm.T;
+  const JobDev& J = sm.J;
+  const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+  const int K = J.K;
+  float* val = a.val_f + T.val_off;
+  const int p = t & 31, g = t >> 5, lane = p, warp = g;
+
+  // Hermitian split of Z = DFT(w + i w r): W = (Z(k) + conj Z(-k)) / 2 into
+  // the table, R = (Z(k) - conj Z(-k)) / 2i into registers.  Table rows >= 32
+  // lie past the FFT buffer and are written at once; rows < 32 wait for every
+  // thread's reads.
+  float2 RX[16], RY[16];
+  float4 wlo[8];
+  static_for<0, 16>([&](auto P) {
+    constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
+    const int k1 = 16 * m + 4 * g + j, k1m = (64 - k1) & 63;
+    float2 w[2], r[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int col = p + 32 * h, colm = (64 - col) & 63;
+      const float2 z = zbuf[swz<64>(k1, col)], zm = zbuf[swz<64>(k1m, colm)];
+      w[h] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      r[h] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    }
+    RX[pi] = make_float2(r[0].x, r[1].x);
+    RY[pi] = make_float2(r[0].y, r[1].y);
+    const float4 slot = make_float4(w[0].x, w[1].x, w[0].y, w[1].y);
+    if constexpr (m >= 2) {
+      Wt[k1 * 64 + p] = slot;
+      Wt[k1 * 64 + p + 32] = swap_pair(slot);
+    } else {
+      wlo[pi] = slot;
+    }
+  });
+  __syncthreads();
+  static_for<0, 8>([&](auto P) {
+    constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
+    const int k1 = 16 * m + 4 * g + j;
+    Wt[k1 * 64 + p] = wlo[pi];
+    Wt[k1 * 64 + p + 32] = swap_pair(wlo[pi]);
+    if (m == 0 && j < 3 && g == 0) {
+      Wt[(k1 + 64) * 64 + p] = wlo[pi];
+      Wt[(k1 + 64) * 64 + p + 32] = swap_pair(wlo[pi]);
+    }
+  });
+  __syncthreads();
+  const float W0 = Wt[0].x;
+  if (!(W0 > 0.f)) {
+    if (t == 0) atomicAdd(&C.q->n_empty, 1);
+    return;
+  }
+  const float gs = J.gamma_f / W0;
+  // key: energy bits with the low 5 bits replaced by 31 - l, l = 2 pi + h the
+  // thread's bin index (increasing with the flat index k1 * 64 + column);
+  // equal keys are resolved by the lowest flat index (lane ballot, then warps)
+  const uint32_t kmask = opaque(~31u);
+  uint32_t bq[2] = {0u, 0u};
+  static_for<0, 16>([&](auto P) {
+    constexpr int pi = decltype(P)::value;
+    float2 e = __fmul2_rn(RX[pi], RX[pi]);
+    e = __ffma2_rn(RY[pi], RY[pi], e);
+    bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+                       make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
+  });
+  uint32_t best = max(bq[0], bq[1]);
+  for (int iter = 0; iter < K; ++iter) {
+    {
+      const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
+      const int l_w = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
+      const int ell = 31 - (int)(wbest & 31u), pw = ell >> 1;
+      const int flat_w = (16 * (pw >> 2) + 4 * warp + (pw & 3)) * 64 + l_w + 32 * (ell & 1);
+      float2 view[32];  // bin l as (Re, Im): register aliases, no copies
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        view[2 * k] = make_float2(RX[k].x, RY[k].x);
+        view[2 * k + 1] = make_float2(RX[k].y, RY[k].y);
+      }
+      const float2 v = select_reg32(view, ell);  // meaningful in lane l_w only
+      st_shared_if(lane == l_w, &sm.xrec[iter & 1][warp],
+                   make_float4(__uint_as_float(wbest), __int_as_float(flat_w), v.x, v.y));
+    }
+    __syncthreads();
+    // Equal keys of two warps name the same thread-local bin, so the lower
+    // warp holds the lower row and the lower flat index: a two-level tree on
+    // the keys alone, keeping the left record on ties.
+    const float4 r0 = sm.xrec[iter & 1][0], r1 = sm.xrec[iter & 1][1];
+    const float4 r2 = sm.xrec[iter & 1][2], r3 = sm.xrec[iter & 1][3];
+    const float4 ra = __float_as_uint(r1.x) > __float_as_uint(r0.x) ? r1 : r0;
+    const float4 rc = __float_as_uint(r3.x) > __float_as_uint(r2.x) ? r3 : r2;
+    const float4 rb = __float_as_uint(rc.x) > __float_as_uint(ra.x) ? rc : ra;
+    const int flat = __float_as_int(rb.y);
+    const int u1 = flat >> 6, u2 = flat & 63;
+    const float dx = gs * rb.z, dy = gs * rb.w;
+    st_shared_if(t == 0, &sm.coef_u[iter], flat);
+    st_shared_if(t == 0, &sm.coef_d[iter], make_float2(dx, dy));
+    if (iter + 1 == K) break;
+    const int d = (p - u2) & 63;
+    const float4* wp[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) wp[m] = Wt + ((16 * m + 4 * g - u1) & 63) * 64 + d;
+    const float2 ndx2 = make_float2(-dx, -dx), dy2 = make_float2(dy, dy), ndy2 = make_float2(-dy, -dy);
+    bq[0] = bq[1] = 0u;
+    static_for<0, 16>([&](auto P) {
+      constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
+      const float4 w = wp[m][j * 64];
+      const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
+      float2 rx = __ffma2_rn(ndx2, wx, RX[pi]);
+      rx = __ffma2_rn(dy2, wy, rx);
+      float2 ry = __ffma2_rn(ndx2, wy, RY[pi]);
+      ry = __ffma2_rn(ndy2, wx, ry);
+      RX[pi] = rx;
+      RY[pi] = ry;
+      float2 e = __fmul2_rn(rx, rx);
+      e = __ffma2_rn(ry, ry, e);
+      bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+                         make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
+    });
+    best = max(bq[0], bq[1]);
+  }
+  __syncthreads();
+  if (a.dbg_useq)
+    for (int k = t; k < K; k += NT) debug_useq(a, CLS_F32_64, id, k, sm.coef_u[k]);
+  eval_and_write<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
+                                      NT);
+}
+
+template <int NWB, int ROWS>
+__device__ __forceinline__ void run_item64(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
+  if constexpr (ROWS == ROWS_PAIRED) item_f32_64p<NWB, ROWS>(a, id, sm, t);
+  else item_f32_64<NWB, ROWS>(a, id, sm, t);
+}
+
 template <int NWB, int ROWS = 128>
 __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS == 96 ? 4 : 3)))
     k_exec_f32_64(const __grid_constant__ ExecArgs a) {
@@ -909,14 +1081,14 @@ __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS
   __syncthreads();
   const ClassArgs& C = a.c[CLS_F32_64];
   if (a.single_item >= 0) {
-    if (blockIdx.x == 0) item_f32_64<NWB, ROWS>(a, a.single_item, sm, t);
+    if (blockIdx.x == 0) run_item64<NWB, ROWS>(a, a.single_item, sm, t);
     return;
   }
   if (a.level_mode) {
     const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x; id < n; id += gridDim.x)
       if (a.level_of[(size_t)CLS_F32_64 * a.level_stride + id] == a.level) {
-        item_f32_64<NWB, ROWS>(a, id, sm, t);
+        run_item64<NWB, ROWS>(a, id, sm, t);
         __syncthreads();
       }
     return;
@@ -929,7 +1101,7 @@ __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS
     __syncthreads();
     const int id = sm.item;
     if (id < 0) break;
-    item_f32_64<NWB, ROWS>(a, id, sm, t);
+    run_item64<NWB, ROWS>(a, id, sm, t);
     __threadfence();
     __syncthreads();
     const int2 it = C.items[id];
@@ -1214,18 +1386,20 @@ __global__ void k_probe(const __grid_constant__ ExecArgs a) {
 // ===========================================================================
 // launchers
 // ===========================================================================
-int g_nwb64 = 4;  // warps per block of the F = 64 executor (4 or 8)
-void set_f64_warps(int nwb) { g_nwb64 = (nwb == 8 || nwb == 2 || nwb == 5) ? nwb : 4; }
+int g_nwb64 = 6;  // layout of the F = 64 executor (warps per block 2, 4, 8; 5, 6: 4 warps)
+void set_f64_warps(int nwb) { g_nwb64 = (nwb == 8 || nwb == 2 || nwb == 4 || nwb == 5) ? nwb : 6; }
 int get_f64_warps() { return g_nwb64; }
 int exec_threads(int cls) {
-  return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? (g_nwb64 == 5 ? 4 : g_nwb64) * 32 : NT64);
+  return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? (g_nwb64 == 5 || g_nwb64 == 6 ? 4 : g_nwb64) * 32 : NT64);
 }
 size_t exec_smem(int cls) {
   if (cls == CLS_F32_32) return SMEM32;
   if (cls == CLS_F32_64)
     return g_nwb64 == 8 ? sizeof(CtaSmem64<8>)
                         : (g_nwb64 == 2 ? sizeof(CtaSmem64<2>)
-                                        : (g_nwb64 == 5 ? sizeof(CtaSmem64<4, 96>) : sizeof(CtaSmem64<4>)));
+                                        : (g_nwb64 == 5 ? sizeof(CtaSmem64<4, 96>)
+                                                        : (g_nwb64 == 6 ? sizeof(CtaSmem64<4, ROWS_PAIRED>)
+                                                                        : sizeof(CtaSmem64<4>))));
   return SMEMD;
 }
 const void* exec_kernel_ptr(int cls) {
@@ -1234,7 +1408,8 @@ const void* exec_kernel_ptr(int cls) {
     return g_nwb64 == 8 ? (const void*)k_exec_f32_64<8>
                         : (g_nwb64 == 2 ? (const void*)k_exec_f32_64<2>
                                         : (g_nwb64 == 5 ? (const void*)k_exec_f32_64<4, 96>
-                                                        : (const void*)k_exec_f32_64<4>));
+                                                        : (g_nwb64 == 6 ? (const void*)k_exec_f32_64<4, ROWS_PAIRED>
+                                                                        : (const void*)k_exec_f32_64<4>)));
   return (const void*)k_exec_f64;
 }
 
@@ -1253,6 +1428,9 @@ cudaError_t exec_setup(int device) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_exec_f32_64<4, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(CtaSmem64<4, 96>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_exec_f32_64<4, ROWS_PAIRED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(CtaSmem64<4, ROWS_PAIRED>));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_exec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEMD);
 }
@@ -1286,6 +1464,8 @@ cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st) {
     k_exec_f32_64<2><<<grid, 64, sizeof(CtaSmem64<2>), st>>>(a);
   else if (cls == CLS_F32_64 && g_nwb64 == 5)
     k_exec_f32_64<4, 96><<<grid, 128, sizeof(CtaSmem64<4, 96>), st>>>(a);
+  else if (cls == CLS_F32_64 && g_nwb64 == 6)
+    k_exec_f32_64<4, ROWS_PAIRED><<<grid, 128, sizeof(CtaSmem64<4, ROWS_PAIRED>), st>>>(a);
   else if (cls == CLS_F32_64)
     k_exec_f32_64<4><<<grid, 128, sizeof(CtaSmem64<4>), st>>>(a);
   else k_exec_f64<<<grid, NT64, SMEMD, st>>>(a);

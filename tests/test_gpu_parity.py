@@ -87,7 +87,7 @@ def _seq_check(oracle_lib, ctx, job, **over):
     assert (got[0]["out"] == ref["out"]).all()
 
 
-@pytest.mark.parametrize("warps", [2, 4, 5, 8])
+@pytest.mark.parametrize("warps", [2, 4, 5, 6, 8])
 def test_fp32_f64_executor_variants(ctx, oracle_lib, warps):
     """Each warps-per-block variant of the F = 64 executor meets the FP32 gate."""
     job = _small_tiled()
