@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="measured requests of the serving leg (0 = skip)")
     ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 6, 8])
+    ap.add_argument("--f32-layout", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--study", default=None, choices=[None, "overlap", "tiling"],
                     help="run a study instead of the benchmark (one JSON line per result)")
@@ -384,6 +385,8 @@ def main():
     ctx.exec_mode(args.mode)
     if args.f64_warps:
         ctx.set_option(fse.OPT_F64_WARPS, args.f64_warps)
+    if args.f32_layout:
+        ctx.set_option(fse.OPT_F32_LAYOUT, args.f32_layout)
     if args.ctas_per_sm:
         ctx.set_option(fse.OPT_CTAS_PER_SM, args.ctas_per_sm)
     keep, cjobs, pix = [], [], 0
@@ -397,7 +400,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     tuned = None
-    if not args.no_autotune and not args.f64_warps and not args.ctas_per_sm and args.mode == "dag":
+    if not args.no_autotune and not args.f64_warps and not args.f32_layout and not args.ctas_per_sm and args.mode == "dag":
         trace = ctx.autotune(cjobs, stream=sptr, reps=3)
         tuned = {"candidates": len(trace),
                  "chosen": {int(c): {"layout": int(l), "ctas_per_sm": int(k), "ms": round(ms, 4)}

@@ -159,6 +159,12 @@ void fse_context_destroy(fse_context_t* ctx);
                                    per SM); 6 = 4 warps, bins paired for the
                                    two-wide FP32 instructions (W table of
                                    16-byte slots, 67 KB); 0 = default (6)      */
+#define FSE_OPT_F32_LAYOUT 8    /* layout of the F = 32 FP32 executor: 1 = one
+                                   spectrum column per lane, 2 = bins paired
+                                   for the two-wide FP32 instructions, 3 = one
+                                   column per lane read in row runs (35-row W
+                                   table, 6 blocks of 2 warps per SM); 0 =
+                                   default (3)                                 */
 #define FSE_OPT_KERNEL_TIMING 6 /* 1 = bracket the iteration kernels of every
                                    call with CUDA events (no synchronisation);
                                    read with fse_context_kernel_times         */
@@ -181,10 +187,10 @@ int32_t fse_context_kernel_times(fse_context_t* ctx, float* ms, int32_t cap);
  * fse_extrapolate_batch; the outputs are written) under candidate launch
  * configurations of each work class present: for F = 64 the executor layout
  * (FSE_OPT_F64_WARPS 6, 4, 5, 2, 8) and the persistent CTAs per SM, for F = 32
- * the CTAs per SM.  Each candidate runs `reps` times (median of the
- * iteration-kernel time); the fastest is applied to the context and, when the
- * context has a tune cache path, written there.  The F = 64 layout is a
- * process-wide setting.  Writes up to cap results as (class, layout,
+ * the layout (FSE_OPT_F32_LAYOUT 3, 1, 2) and the CTAs per SM.  Each candidate
+ * runs `reps` times (median of the iteration-kernel time); the fastest is
+ * applied to the context and, when the context has a tune cache path, written
+ * there.  The layouts are process-wide settings.  Writes up to cap results as (class, layout,
  * ctas_per_sm, milliseconds) quadruples into `trace` (may be NULL) and
  * returns how many candidates ran, or a negative status.
  */

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfse.so")
 OK, EINVAL, EDEGENERATE, ENOMEM, EBUSY, ETIMEOUT, ECUDA, ENOTFOUND, ECANCELLED = 0, -1, -2, -3, -4, -5, -6, -7, -8
 ORDER = {"phased": 0, "raster": 1, "independent": 2}
 TILING = {"alg1": 0, "vertical": 1}
-OPT_EXEC_MODE, OPT_TIMEOUT_MS, OPT_CTAS_PER_SM, OPT_USE_GRAPH, OPT_DEBUG_CAPTURE, OPT_KERNEL_TIMING, OPT_F64_WARPS = 1, 2, 3, 4, 5, 6, 7
+OPT_EXEC_MODE, OPT_TIMEOUT_MS, OPT_CTAS_PER_SM, OPT_USE_GRAPH, OPT_DEBUG_CAPTURE, OPT_KERNEL_TIMING = 1, 2, 3, 4, 5, 6
+OPT_F64_WARPS, OPT_F32_LAYOUT = 7, 8
 EXEC = {"dag": 0, "levels": 1, "per_block": 2}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 

@@ -18,7 +18,8 @@ using fse::Context;
 namespace fse {
 
 // Autotuner cache: the GPU name on the first line, then one line per work
-// class "cls ctas_per_sm layout" (layout: FSE_OPT_F64_WARPS for class 1).
+// class "cls ctas_per_sm layout" (layout: FSE_OPT_F32_LAYOUT for class 0,
+// FSE_OPT_F64_WARPS for class 1).
 // A missing or foreign file is ignored.
 void tune_load(Context* c) {
   FILE* f = fopen(c->tune_path.c_str(), "r");
@@ -34,6 +35,7 @@ void tune_load(Context* c) {
         if (k < 0 || k >= MAX_CLS || v <= 0) continue;
         c->tuned_ctas[k] = v;
         if (k == CLS_F32_64 && (lay == 2 || lay == 4 || lay == 5 || lay == 6 || lay == 8)) set_f64_warps(lay);
+        if (k == CLS_F32_32 && lay >= 1 && lay <= 3) set_f32_layout(lay);
       }
     }
   }
@@ -48,7 +50,7 @@ static void tune_save(Context* c) {
   cudaGetDeviceProperties(&prop, c->device);
   fprintf(f, "%s\n", prop.name);
   for (int k = 0; k < MAX_CLS; ++k)
-    if (c->tuned_ctas[k] > 0) fprintf(f, "%d %d %d\n", k, c->tuned_ctas[k], k == CLS_F32_64 ? get_f64_warps() : 0);
+    if (c->tuned_ctas[k] > 0) fprintf(f, "%d %d %d\n", k, c->tuned_ctas[k], k == CLS_F32_64 ? get_f64_warps() : (k == CLS_F32_32 ? get_f32_layout() : 0));
   fclose(f);
 }
 
@@ -120,16 +122,24 @@ int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int 
   }
   if (present[CLS_F32_32] && rc == FSE_OK) {
     double best = 1e30;
-    int best_ctas = 0;
-    const int occ = c->occupancy[CLS_F32_32];
-    for (int k = occ; k >= 1 && k >= occ - 3 && rc == FSE_OK; --k) {
-      double ms;
-      rc = time_cfg(CLS_F32_32, 0, k, &ms);
-      if (rc == FSE_OK && ms < best) {
-        best = ms;
-        best_ctas = k;
+    int best_lay = get_f32_layout(), best_ctas = 0;
+    const int layouts[3] = {3, 1, 2};
+    for (int li = 0; li < 3 && rc == FSE_OK; ++li) {
+      set_f32_layout(layouts[li]);
+      c->occupancy[CLS_F32_32] = occupancy_of(CLS_F32_32);
+      const int occ = c->occupancy[CLS_F32_32];
+      for (int k = occ; k >= 1 && k >= occ - 3 && rc == FSE_OK; --k) {
+        double ms;
+        rc = time_cfg(CLS_F32_32, layouts[li], k, &ms);
+        if (rc == FSE_OK && ms < best) {
+          best = ms;
+          best_lay = layouts[li];
+          best_ctas = k;
+        }
       }
     }
+    set_f32_layout(best_lay);
+    c->occupancy[CLS_F32_32] = occupancy_of(CLS_F32_32);
     c->tuned_ctas[CLS_F32_32] = best_ctas;
   }
   c->exec_mode = saved_mode;
@@ -248,6 +258,17 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
     case FSE_OPT_DEBUG_CAPTURE:
       c->debug = value != 0;
       return FSE_OK;
+    case FSE_OPT_F32_LAYOUT: {
+      if (value < 0 || value > 3) return fse::fail(FSE_EINVAL, "f32 layout");
+      fse::set_f32_layout(value == 0 ? 3 : (int)value);
+      int nb = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fse::exec_kernel_ptr(fse::CLS_F32_32),
+                                                    fse::exec_threads(fse::CLS_F32_32),
+                                                    fse::exec_smem(fse::CLS_F32_32));
+      c->occupancy[fse::CLS_F32_32] = nb > 0 ? nb : 1;
+      c->graph_jobs.clear();
+      return FSE_OK;
+    }
     case FSE_OPT_F64_WARPS: {
       if (value != 0 && value != 2 && value != 4 && value != 5 && value != 6 && value != 8)
         return fse::fail(FSE_EINVAL, "f64 warps");

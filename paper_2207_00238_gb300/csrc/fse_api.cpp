@@ -205,10 +205,11 @@ static int context_init(Context** out, int device, size_t arena_bytes, char* ali
   if (tune_path) {
     c->tune_path = tune_path;
     tune_load(c);
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(CLS_F32_64),
-                                                  exec_threads(CLS_F32_64), exec_smem(CLS_F32_64));
-    c->occupancy[CLS_F32_64] = std::max(1, nb);
+    for (int k = 0; k < MAX_CLS; ++k) {  // the cache may have changed a layout
+      int nb = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(k), exec_threads(k), exec_smem(k));
+      c->occupancy[k] = std::max(1, nb);
+    }
   }
   *out = c;
   return FSE_OK;

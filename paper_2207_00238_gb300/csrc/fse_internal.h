@@ -102,6 +102,8 @@ cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st);
 int exec_threads(int cls);
 void set_f64_warps(int nwb);  // warps per block of the F = 64 executor (4 or 8)
 int get_f64_warps();
+void set_f32_layout(int lay);  // F = 32 executor: 1 = one column per lane, 2 = paired bins, 3 = row runs
+int get_f32_layout();
 size_t exec_smem(int cls);
 cudaError_t exec_setup(int device);  // smem opt-in for every executor kernel
 const void* exec_kernel_ptr(int cls);

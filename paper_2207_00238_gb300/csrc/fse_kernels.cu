@@ -164,34 +164,37 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
     delta = J.delta;
   }
   const bool use_done = J.order != ORDER_INDEPENDENT;
-  constexpr int U = 8;  // pixels per thread whose loads are in flight together
-  for (int e0 = t; e0 < S * S; e0 += U * nthr) {
+  // Thread t owns support column n = t mod F and the rows m0, m0 + mstep, ...
+  // Out-of-tile pixels load from the tile's first pixel and are masked off,
+  // so every load of a batch issues unconditionally, back to back.
+  const int n = t & (F - 1), m0 = t / F, mstep = nthr / F;
+  const int tx = ox + n;
+  const bool col_in = n < S && tx >= 0 && tx < T.ew;
+  const int ew = T.ew, eh = T.eh;
+  const size_t pitch = J.pitch, g0 = (size_t)T.ey * pitch + T.ex;
+  const uint8_t* mask = J.mask;
+  const uint8_t* image = J.image;
+  constexpr int U = 8;  // rows whose loads are in flight together
+  if (n >= S) return;
+  for (int mb = m0; mb < S; mb += U * mstep) {
     uint8_t mk[U], px[U];
     real wi[U], v[U];
     bool in[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {  // all loads first
-      const int e = e0 + u * nthr;
-      const int m = e / S, n = e - m * S;
-      const int ty = oy + m, tx = ox + n;
-      in[u] = e < S * S && ty >= 0 && ty < T.eh && tx >= 0 && tx < T.ew;
-      mk[u] = 1;
-      px[u] = 0;
-      wi[u] = 0;
-      v[u] = 0;
-      if (in[u]) {
-        const size_t gi = (size_t)(T.ey + ty) * J.pitch + (T.ex + tx);
-        wi[u] = __ldg(wiso + e);
-        mk[u] = __ldg(J.mask + gi);
-        px[u] = __ldg(J.image + gi);
-        v[u] = __ldcg(val + (size_t)ty * T.ew + tx);
-      }
+    for (int u = 0; u < U; ++u) {
+      const int m = mb + u * mstep, ty = oy + m;
+      in[u] = col_in && m < S && ty >= 0 && ty < eh;
+      const size_t gi = in[u] ? g0 + (size_t)ty * pitch + tx : g0;
+      const size_t vi = in[u] ? (size_t)ty * ew + tx : 0;
+      wi[u] = __ldg(wiso + (m < S ? m * S + n : n));
+      mk[u] = __ldg(mask + gi);
+      px[u] = __ldg(image + gi);
+      v[u] = __ldcg(val + vi);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * nthr;
-      if (e >= S * S) break;
-      const int m = e / S, n = e - m * S;
+      const int m = mb + u * mstep;
+      if (m >= S) break;
       real wv = 0, zr = 0;
       if (in[u]) {
         if (mk[u] == 0) {
@@ -509,6 +512,9 @@ __device__ __forceinline__ void st_shared_if(bool pred, void* p, int v) {
                ::"r"((unsigned)pred), "r"(a), "r"(v) : "memory");
 }
 
+// Exchanges the halves of both pairs of a (re, re', im, im') slot.
+__device__ __forceinline__ float4 swap_pair(float4 v) { return make_float4(v.y, v.x, v.w, v.z); }
+
 // Three-input unsigned max.
 __device__ __forceinline__ uint32_t max3u(uint32_t a, uint32_t b, uint32_t c) {
   return max(a, max(b, c));
@@ -540,8 +546,12 @@ struct alignas(16) WarpSmem32 {
 constexpr int NW32 = 2;  // warps (independent workers) per CTA
 constexpr size_t SMEM32 = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32);
 
-__device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem32& sm, const float2* tw,
-                            int lane) {
+// Prologue of one F = 32 block: descriptors into shared memory, the support
+// staged into zbuf (32 x 32, swizzled), row FFTs in place, then the column
+// FFTs into registers: x[k1] = Z(k1, lane).
+template <class WS>
+__device__ __forceinline__ void stage_fft32(const ExecArgs& a, int id, WS& sm, float2* zbuf, int lane,
+                                            float2 (&x)[32]) {
   const ClassArgs& C = a.c[CLS_F32_32];
   const int2 it = C.items[id];
   copy_desc(&sm.T, a.tiles + it.x, lane, 32);
@@ -551,15 +561,11 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
-  const int S = J.S, K = J.K;
+  const int S = J.S;
   float* val = a.val_f + T.val_off;
   if (lane == 0) debug_record(a, CLS_F32_32, id, T, it.x, I, Jb);
-  float2* zbuf = sm.Wd + 32 * 32;
-
-  // stage -> rows 32..63 (swizzled F x F buffer)
   stage_support<32, float, float2>(T, J, val, I, Jb, zbuf, lane, 32);
   __syncwarp();
-  float2 x[32];
   // row FFTs: lane m transforms support row m
   if (lane < S) {
 #pragma unroll
@@ -569,11 +575,25 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
     for (int n = 0; n < 32; ++n) zbuf[swz<32>(lane, n)] = x[n];
   }
   __syncwarp();
-  // column FFTs: lane l transforms column l -> x[k1] = Z(k1, l)
+  // column FFTs: lane l transforms column l
 #pragma unroll
   for (int m = 0; m < 32; ++m) x[m] = m < S ? zbuf[swz<32>(m, lane)] : make_float2(0.f, 0.f);
   fft_reg<32>(x);
   __syncwarp();
+}
+
+__device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem32& sm, const float2* tw,
+                            int lane) {
+  const ClassArgs& C = a.c[CLS_F32_32];
+  float2 x[32];
+  // stage -> rows 32..63 (swizzled F x F buffer)
+  stage_fft32(a, id, sm, sm.Wd + 32 * 32, lane, x);
+  const int2 it = C.items[id];
+  const TileDev& T = sm.T;
+  const JobDev& J = sm.J;
+  const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+  const int K = J.K;
+  float* val = a.val_f + T.val_off;
   // Hermitian split: W = (Z(k) + conj Z(-k))/2, R = (Z(k) - conj Z(-k))/(2i)
   const int src = (32 - lane) & 31;
 #pragma unroll
@@ -657,29 +677,290 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
                                        32);
 }
 
-__global__ void __launch_bounds__(NW32 * 32, 5) k_exec_f32_32(const __grid_constant__ ExecArgs a) {
+// ---------------------------------------------------------------------------
+// Paired-bin layout of the F = 32 executor.  Lane L = 16 h + p owns the bins
+// (k1, p) and (k1, p + 16) for the 16 rows k1 = 8 m + 4 h + j (m, j = 0..3),
+// as pairs RX[4m + j] = (Re R(k1, p), Re R(k1, p + 16)), RY likewise.  W is a
+// table of 16-byte slots (Re W(r, d), Re W(r, d ^ 16), Im W(r, d),
+// Im W(r, d ^ 16)) with rows 0..2 repeated as rows 32..34; rows 0..15 double
+// as the FFT buffer.  Equal keys name the same (m, j, column half), where the
+// lower lane holds the lower row, then the lower column: the lowest lane is
+// the lowest flat index.
+// ---------------------------------------------------------------------------
+struct alignas(16) WarpSmem32P {
+  float4 Wt[35 * 32];
+  float2 coef_d[KMAX];
+  int32_t coef_u[KMAX];
+  float red[32];
+  TileDev T;
+  JobDev J;
+};
+
+__device__ __forceinline__ void item_f32_32p(const ExecArgs& a, int id, WarpSmem32P& sm, const float2* tw,
+                                             int lane) {
+  const ClassArgs& C = a.c[CLS_F32_32];
+  float2* zbuf = reinterpret_cast<float2*>(sm.Wt);
+  float4* Wt = sm.Wt;
+  float2 x[32];
+  stage_fft32(a, id, sm, zbuf, lane, x);
+  const int2 it = C.items[id];
+  const TileDev& T = sm.T;
+  const JobDev& J = sm.J;
+  const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+  const int K = J.K;
+  float* val = a.val_f + T.val_off;
+  // the column spectra back to the buffer, then the Hermitian split of the
+  // pairs this lane owns
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1) zbuf[swz<32>(k1, lane)] = x[k1];
+  __syncwarp();
+  const int p = lane & 15, h = lane >> 4;
+  float2 RX[16], RY[16];
+  float4 wlo[8];
+  static_for<0, 16>([&](auto P) {
+    constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
+    const int k1 = 8 * m + 4 * h + j, k1m = (32 - k1) & 31;
+    float2 w[2], r[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int col = p + 16 * c, colm = (32 - col) & 31;
+      const float2 z = zbuf[swz<32>(k1, col)], zm = zbuf[swz<32>(k1m, colm)];
+      w[c] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      r[c] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    }
+    RX[pi] = make_float2(r[0].x, r[1].x);
+    RY[pi] = make_float2(r[0].y, r[1].y);
+    const float4 slot = make_float4(w[0].x, w[1].x, w[0].y, w[1].y);
+    if constexpr (m >= 2) {  // rows 16..31: past the FFT buffer
+      Wt[k1 * 32 + p] = slot;
+      Wt[k1 * 32 + p + 16] = swap_pair(slot);
+    } else {
+      wlo[pi] = slot;
+    }
+  });
+  __syncwarp();
+  static_for<0, 8>([&](auto P) {
+    constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
+    const int k1 = 8 * m + 4 * h + j;
+    Wt[k1 * 32 + p] = wlo[pi];
+    Wt[k1 * 32 + p + 16] = swap_pair(wlo[pi]);
+    if (m == 0 && j < 3 && h == 0) {
+      Wt[(k1 + 32) * 32 + p] = wlo[pi];
+      Wt[(k1 + 32) * 32 + p + 16] = swap_pair(wlo[pi]);
+    }
+  });
+  __syncwarp();
+  const float W0 = Wt[0].x;
+  if (!(W0 > 0.f)) {  // no usable pixel in the support
+    if (lane == 0) atomicAdd(&C.q->n_empty, 1);
+    return;
+  }
+  const float gs = J.gamma_f / W0;
+  // key: energy bits with the low 5 bits replaced by 31 - l, l = 2 pi + c
+  const uint32_t kmask = opaque(~31u);
+  uint32_t bq[2] = {0u, 0u};
+  static_for<0, 16>([&](auto P) {
+    constexpr int pi = decltype(P)::value;
+    float2 e = __fmul2_rn(RX[pi], RX[pi]);
+    e = __ffma2_rn(RY[pi], RY[pi], e);
+    bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+                       make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
+  });
+  uint32_t best = max(bq[0], bq[1]);
+  for (int iter = 0; iter < K; ++iter) {
+    const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
+    const int l_w = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
+    const int ell = 31 - (int)(wbest & 31u), pw = ell >> 1;
+    const int u1 = 8 * (pw >> 2) + 4 * (l_w >> 4) + (pw & 3);
+    const int u2 = (l_w & 15) + 16 * (ell & 1);
+    float2 view[32];  // bin l as (Re, Im): register aliases, no copies
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      view[2 * k] = make_float2(RX[k].x, RY[k].x);
+      view[2 * k + 1] = make_float2(RX[k].y, RY[k].y);
+    }
+    const float2 v = select_reg32(view, ell);
+    const float rux = __shfl_sync(0xffffffffu, v.x, l_w);
+    const float ruy = __shfl_sync(0xffffffffu, v.y, l_w);
+    const float dx = gs * rux, dy = gs * ruy;
+    st_shared_if(lane == 0, &sm.coef_u[iter], u1 * 32 + u2);
+    st_shared_if(lane == 0, &sm.coef_d[iter], make_float2(dx, dy));
+    if (iter + 1 == K) break;
+    const int d = (p - u2) & 31;
+    const float4* wp[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) wp[m] = Wt + ((8 * m + 4 * h - u1) & 31) * 32 + d;
+    const float2 ndx2 = make_float2(-dx, -dx), dy2 = make_float2(dy, dy), ndy2 = make_float2(-dy, -dy);
+    bq[0] = bq[1] = 0u;
+    static_for<0, 16>([&](auto P) {
+      constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
+      const float4 w = wp[m][j * 32];
+      const float2 wx = make_float2(w.x, w.y), wy = make_float2(w.z, w.w);
+      float2 rx = __ffma2_rn(ndx2, wx, RX[pi]);
+      rx = __ffma2_rn(dy2, wy, rx);
+      float2 ry = __ffma2_rn(ndx2, wy, RY[pi]);
+      ry = __ffma2_rn(ndy2, wx, ry);
+      RX[pi] = rx;
+      RY[pi] = ry;
+      float2 e = __fmul2_rn(rx, rx);
+      e = __ffma2_rn(ry, ry, e);
+      bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+                         make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
+    });
+    best = max(bq[0], bq[1]);
+  }
+  __syncwarp();
+  if (a.dbg_useq)
+    for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
+  eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
+                                       32);
+}
+constexpr size_t SMEM32P = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32P);
+
+// ---------------------------------------------------------------------------
+// Run layout of the F = 32 executor: lane l owns column l and all 32 rows, as
+// the column layout does, but reads its rows in eight runs of four, each from
+// its own base row, so W needs only rows 0..2 repeated (35 rows, 8.75 KB per
+// warp) and the table overlays the FFT buffer.  Same arithmetic and keys as
+// the column layout; more warps fit on an SM.
+// ---------------------------------------------------------------------------
+struct alignas(16) WarpSmem32R {
+  float2 Wd[35 * 32];  // W rows 0..31, rows 32..34 repeat rows 0..2; rows 0..31 double as FFT buffer
+  float2 coef_d[KMAX];
+  int32_t coef_u[KMAX];
+  float red[32];
+  TileDev T;
+  JobDev J;
+};
+
+__device__ __forceinline__ void item_f32_32r(const ExecArgs& a, int id, WarpSmem32R& sm, const float2* tw,
+                                             int lane) {
+  const ClassArgs& C = a.c[CLS_F32_32];
+  float2 x[32];
+  stage_fft32(a, id, sm, sm.Wd, lane, x);
+  const int2 it = C.items[id];
+  const TileDev& T = sm.T;
+  const JobDev& J = sm.J;
+  const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+  const int K = J.K;
+  float* val = a.val_f + T.val_off;
+  // Hermitian split from registers (the FFT buffer is no longer read)
+  const int src = (32 - lane) & 31;
+#pragma unroll
+  for (int j = 0; j <= 16; ++j) {
+    const int j2 = (32 - j) & 31;
+    float2 zm, zm2;
+    zm.x = __shfl_sync(0xffffffffu, x[j2].x, src);
+    zm.y = __shfl_sync(0xffffffffu, x[j2].y, src);
+    zm2.x = __shfl_sync(0xffffffffu, x[j].x, src);
+    zm2.y = __shfl_sync(0xffffffffu, x[j].y, src);
+    const float2 z = x[j], z2 = x[j2];
+    const float2 w = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+    sm.Wd[j * 32 + lane] = w;
+    if (j < 3) sm.Wd[(j + 32) * 32 + lane] = w;
+    x[j] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    if (j2 != j) {
+      const float2 w2 = make_float2(0.5f * (z2.x + zm2.x), 0.5f * (z2.y - zm2.y));
+      sm.Wd[j2 * 32 + lane] = w2;
+      x[j2] = make_float2(0.5f * (z2.y + zm2.y), 0.5f * (zm2.x - z2.x));
+    }
+  }
+  __syncwarp();
+  const float W0 = sm.Wd[0].x;
+  if (!(W0 > 0.f)) {  // no usable pixel in the support
+    if (lane == 0) atomicAdd(&C.q->n_empty, 1);
+    return;
+  }
+  const float gs = J.gamma_f / W0;
+  float2(&R)[32] = x;
+  // key: energy bits with the low 5 bits replaced by 31 - row; equal keys go
+  // to the lowest lane, i.e. the lowest flat index
+  const uint32_t kmask = opaque(0xFFFFFFE0u);
+  uint32_t bq[2] = {0u, 0u};
+  static_for<0, 16>([&](auto h) {
+    constexpr int j = 2 * decltype(h)::value;
+    const float e0 = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
+    const float e1 = fmaf(R[j + 1].y, R[j + 1].y, R[j + 1].x * R[j + 1].x);
+    bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<31u - j>(e0, kmask),
+                             make_key<30u - j>(e1, kmask));
+  });
+  uint32_t best = max(bq[0], bq[1]);
+  for (int iter = 0; iter < K; ++iter) {
+    const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
+    const int u2 = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
+    const int u1 = 31 - (int)(wbest & 31u);
+    const int flat = u1 * 32 + u2;
+    const float2 v = select_reg<32>(R, u1);
+    const float rux = __shfl_sync(0xffffffffu, v.x, u2);
+    const float ruy = __shfl_sync(0xffffffffu, v.y, u2);
+    const float dx = gs * rux, dy = gs * ruy;
+    st_shared_if(lane == 0, &sm.coef_u[iter], flat);
+    st_shared_if(lane == 0, &sm.coef_d[iter], make_float2(dx, dy));
+    if (iter + 1 == K) break;
+    const int d = (lane - u2) & 31;
+    const float2* wp[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) wp[q] = sm.Wd + ((4 * q - u1) & 31) * 32 + d;
+    const float ndx = -dx, ndy = -dy;
+    bq[0] = bq[1] = 0u;
+    static_for<0, 16>([&](auto h) {
+      constexpr int j = 2 * decltype(h)::value;
+      float e[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float2 w = wp[(j + k) >> 2][((j + k) & 3) * 32];
+        float rx = fmaf(ndx, w.x, R[j + k].x);
+        rx = fmaf(dy, w.y, rx);
+        float ry = fmaf(ndx, w.y, R[j + k].y);
+        ry = fmaf(ndy, w.x, ry);
+        R[j + k] = make_float2(rx, ry);
+        e[k] = fmaf(ry, ry, rx * rx);
+      }
+      bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<31u - j>(e[0], kmask),
+                               make_key<30u - j>(e[1], kmask));
+    });
+    best = max(bq[0], bq[1]);
+  }
+  __syncwarp();
+  if (a.dbg_useq)
+    for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
+  eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
+                                       32);
+}
+constexpr size_t SMEM32R = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32R);
+
+template <class WS>
+__device__ __forceinline__ void run_item32(const ExecArgs& a, int id, WS& sm, const float2* tw, int lane) {
+  if constexpr (std::is_same<WS, WarpSmem32P>::value) item_f32_32p(a, id, sm, tw, lane);
+  else if constexpr (std::is_same<WS, WarpSmem32R>::value) item_f32_32r(a, id, sm, tw, lane);
+  else item_f32_32(a, id, sm, tw, lane);
+}
+
+template <class WS>
+__global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32R>::value ? 6 : 5)
+    k_exec_f32_32(const __grid_constant__ ExecArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
-  WarpSmem32* wsm = reinterpret_cast<WarpSmem32*>(smem_raw + 64 * sizeof(float2));
+  WS* wsm = reinterpret_cast<WS*>(smem_raw + 64 * sizeof(float2));
   for (int q = threadIdx.x; q < 64; q += blockDim.x) tw[q] = make_float2(c_twf[q].x, -c_twf[q].y);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpSmem32& sm = wsm[warp];
+  WS& sm = wsm[warp];
   const ClassArgs& C = a.c[CLS_F32_32];
   if (a.single_item >= 0) {
-    if (blockIdx.x == 0 && warp == 0) item_f32_32(a, a.single_item, sm, tw, lane);
+    if (blockIdx.x == 0 && warp == 0) run_item32(a, a.single_item, sm, tw, lane);
     return;
   }
   if (a.level_mode) {
     const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x * NW32 + warp; id < n; id += gridDim.x * NW32)
-      if (a.level_of[(size_t)CLS_F32_32 * a.level_stride + id] == a.level) item_f32_32(a, id, sm, tw, lane);
+      if (a.level_of[(size_t)CLS_F32_32 * a.level_stride + id] == a.level) run_item32(a, id, sm, tw, lane);
     return;
   }
   for (;;) {
     const int id = queue_pop_warp(C, a.timeout_ns, lane);
     if (id < 0) break;
-    item_f32_32(a, id, sm, tw, lane);
+    run_item32(a, id, sm, tw, lane);
     __threadfence();
     __syncwarp();
     const int2 it = C.items[id];
@@ -926,8 +1207,6 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
 // repeats rows 0..2 as rows 64..66 so a run that wraps stays contiguous.
 // ---------------------------------------------------------------------------
 constexpr int ROWS_PAIRED = 134;  // 67 rows of 64 float4 slots, counted in float2 rows
-
-__device__ __forceinline__ float4 swap_pair(float4 v) { return make_float4(v.y, v.x, v.w, v.z); }
 
 template <int NWB, int ROWS>
 __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
@@ -1389,11 +1668,14 @@ __global__ void k_probe(const __grid_constant__ ExecArgs a) {
 int g_nwb64 = 6;  // layout of the F = 64 executor (warps per block 2, 4, 8; 5, 6: 4 warps)
 void set_f64_warps(int nwb) { g_nwb64 = (nwb == 8 || nwb == 2 || nwb == 4 || nwb == 5) ? nwb : 6; }
 int get_f64_warps() { return g_nwb64; }
+int g_lay32 = 3;  // layout of the F = 32 executor: 1 = one column per lane, 2 = paired bins, 3 = row runs
+void set_f32_layout(int lay) { g_lay32 = (lay == 1 || lay == 2) ? lay : 3; }
+int get_f32_layout() { return g_lay32; }
 int exec_threads(int cls) {
   return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? (g_nwb64 == 5 || g_nwb64 == 6 ? 4 : g_nwb64) * 32 : NT64);
 }
 size_t exec_smem(int cls) {
-  if (cls == CLS_F32_32) return SMEM32;
+  if (cls == CLS_F32_32) return g_lay32 == 1 ? SMEM32 : (g_lay32 == 2 ? SMEM32P : SMEM32R);
   if (cls == CLS_F32_64)
     return g_nwb64 == 8 ? sizeof(CtaSmem64<8>)
                         : (g_nwb64 == 2 ? sizeof(CtaSmem64<2>)
@@ -1403,7 +1685,10 @@ size_t exec_smem(int cls) {
   return SMEMD;
 }
 const void* exec_kernel_ptr(int cls) {
-  if (cls == CLS_F32_32) return (const void*)k_exec_f32_32;
+  if (cls == CLS_F32_32)
+    return g_lay32 == 1   ? (const void*)k_exec_f32_32<WarpSmem32>
+           : g_lay32 == 2 ? (const void*)k_exec_f32_32<WarpSmem32P>
+                          : (const void*)k_exec_f32_32<WarpSmem32R>;
   if (cls == CLS_F32_64)
     return g_nwb64 == 8 ? (const void*)k_exec_f32_64<8>
                         : (g_nwb64 == 2 ? (const void*)k_exec_f32_64<2>
@@ -1415,7 +1700,12 @@ const void* exec_kernel_ptr(int cls) {
 
 cudaError_t exec_setup(int device) {
   (void)device;
-  cudaError_t e = cudaFuncSetAttribute(k_exec_f32_32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM32);
+  cudaError_t e = cudaFuncSetAttribute(k_exec_f32_32<WarpSmem32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SMEM32);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_exec_f32_32<WarpSmem32P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM32P);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_exec_f32_32<WarpSmem32R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM32R);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_exec_f32_64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(CtaSmem64<4>));
@@ -1457,7 +1747,9 @@ cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st) {
 
 cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
-  if (cls == CLS_F32_32) k_exec_f32_32<<<grid, NW32 * 32, SMEM32, st>>>(a);
+  if (cls == CLS_F32_32 && g_lay32 == 1) k_exec_f32_32<WarpSmem32><<<grid, NW32 * 32, SMEM32, st>>>(a);
+  else if (cls == CLS_F32_32 && g_lay32 == 2) k_exec_f32_32<WarpSmem32P><<<grid, NW32 * 32, SMEM32P, st>>>(a);
+  else if (cls == CLS_F32_32) k_exec_f32_32<WarpSmem32R><<<grid, NW32 * 32, SMEM32R, st>>>(a);
   else if (cls == CLS_F32_64 && g_nwb64 == 8)
     k_exec_f32_64<8><<<grid, 256, sizeof(CtaSmem64<8>), st>>>(a);
   else if (cls == CLS_F32_64 && g_nwb64 == 2)

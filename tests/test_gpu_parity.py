@@ -87,6 +87,35 @@ def _seq_check(oracle_lib, ctx, job, **over):
     assert (got[0]["out"] == ref["out"]).all()
 
 
+@pytest.mark.parametrize("layout", [1, 2, 3])
+@pytest.mark.parametrize("case", ["plain_64", "defects_small"])
+def test_fp32_f32_executor_layouts(ctx, oracle_lib, layout, case):
+    """Each layout of the F = 32 executor meets the FP32 gate."""
+    job = CASES[case]()
+    ctx.set_option(fse.OPT_F32_LAYOUT, layout)
+    try:
+        got, _ = run_gpu(ctx, [job])
+    finally:
+        ctx.set_option(fse.OPT_F32_LAYOUT, 0)
+    _fp32_check(oracle_lib, job, got[0])
+
+
+def test_f32_run_layout_matches_column_layout(ctx):
+    """The row-run layout of the F = 32 executor does the column layout's
+    arithmetic in the same order: identical bytes and model values."""
+    jobs = [CASES["plain_64"](), CASES["defects_small"]()]
+    res = {}
+    for layout in (1, 3):
+        ctx.set_option(fse.OPT_F32_LAYOUT, layout)
+        try:
+            res[layout], _ = run_gpu(ctx, jobs)
+        finally:
+            ctx.set_option(fse.OPT_F32_LAYOUT, 0)
+    for a, b in zip(res[1], res[3]):
+        assert (a["out"] == b["out"]).all()
+        np.testing.assert_array_equal(a["g"], b["g"])
+
+
 @pytest.mark.parametrize("warps", [2, 4, 5, 6, 8])
 def test_fp32_f64_executor_variants(ctx, oracle_lib, warps):
     """Each warps-per-block variant of the F = 64 executor meets the FP32 gate."""
