@@ -373,11 +373,6 @@ __device__ __forceinline__ void debug_useq(const ExecArgs& a, int cls, int id, i
   a.dbg_useq[((size_t)cls * a.dbg_cap + id) * KMAX + it] = u;
 }
 
-// Argmax key of one bin: the energy's float bits with the low 10 (F = 32) or
-// 12 (F = 64) mantissa bits replaced by the inverted flat index, so that an
-// integer max picks the largest energy and, among energies equal to the
-// kept precision, the lowest flat index k1*F + k2.
-
 // Register select v = R[i] for a warp-uniform i: one indirect branch through a
 // jump table (brx.idx) to a pair of moves, so the spectrum stays in registers
 // and the select costs one branch instead of a compare tree.
