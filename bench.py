@@ -314,6 +314,18 @@ def run_study(args):
         d = out.astype(np.float64) - img.astype(np.float64)
         return 10 * np.log10(255.0 ** 2 / np.mean(d * d))
 
+    def ssim_all(out, img):
+        # mean SSIM (Wang, Bovik, Sheikh, Simoncelli 2004): Gaussian window
+        # sigma 1.5 (11 x 11), C1 = (0.01 * 255)^2, C2 = (0.03 * 255)^2
+        from scipy.ndimage import gaussian_filter
+        x, y = out.astype(np.float64), img.astype(np.float64)
+        g = lambda z: gaussian_filter(z, 1.5, truncate=3.5)
+        mx, my = g(x), g(y)
+        sxx, syy, sxy = g(x * x) - mx * mx, g(y * y) - my * my, g(x * y) - mx * my
+        c1, c2 = (0.01 * 255) ** 2, (0.03 * 255) ** 2
+        m = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+        return float(m.mean())
+
     if args.study == "overlap":
         for loss in (0.14, 0.62):
             img, mask = paper_scale_jobs(loss)
@@ -322,15 +334,18 @@ def run_study(args):
             out_d = torch.empty_like(img_d)
             base = synth.params(4, 14, 32, 100)
             st = run(img_d, msk_d, out_d, dict(base, n_tiles=1, overlap=0))
-            ref = psnr_all(out_d.cpu().numpy(), img)
+            o = out_d.cpu().numpy()
+            ref, ref_s = psnr_all(o, img), ssim_all(o, img)
             print(json.dumps({"study": "overlap", "loss": loss, "n_tiles": 1, "overlap": 0,
-                              "psnr_db": ref, "lost_blocks": st["lost_blocks"],
+                              "psnr_db": ref, "ssim": ref_s, "lost_blocks": st["lost_blocks"],
                               "exec_ms": st["exec_ms"]}), flush=True)
             for d in (0, 1, 2, 4, 8, 16, 24, 32, 48, 64, 96):
                 st = run(img_d, msk_d, out_d, dict(base, n_tiles=32, overlap=d))
-                ps = psnr_all(out_d.cpu().numpy(), img)
+                o = out_d.cpu().numpy()
+                ps, ss = psnr_all(o, img), ssim_all(o, img)
                 print(json.dumps({"study": "overlap", "loss": loss, "n_tiles": 32, "overlap": d,
-                                  "psnr_db": ps, "delta_vs_untiled_db": ps - ref,
+                                  "psnr_db": ps, "delta_vs_untiled_db": ps - ref, "ssim": ss,
+                                  "delta_ssim_vs_untiled": ss - ref_s,
                                   "lost_blocks": st["lost_blocks"], "exec_ms": st["exec_ms"]}),
                       flush=True)
     else:
