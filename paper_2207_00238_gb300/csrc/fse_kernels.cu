@@ -311,8 +311,8 @@ __device__ __forceinline__ void bar() {
 // Model evaluation at the block's b x b pixels and write-back (all executors).
 // coef_u / coef_d hold the K selected (u, Delta) pairs; tw[q] = exp(+2 pi i q/64).
 // Threads split the K terms when the block has fewer pixels than threads.
-template <bool CTA, typename real, typename real2>
-__device__ __forceinline__ void eval_and_write(const TileDev& T, const JobDev& J, real* val, int I, int Jb,
+template <bool CTA, int C, typename real, typename real2>
+__device__ __forceinline__ void eval_body(const TileDev& T, const JobDev& J, real* val, int I, int Jb,
                                const int* coef_u, const real2* coef_d, const real2* tw,
                                real* red, int t, int nthr) {
   const int b = J.b, np = b * b, K = J.K, F = J.F, B = J.B;
@@ -320,25 +320,30 @@ __device__ __forceinline__ void eval_and_write(const TileDev& T, const JobDev& J
   const int nsplit = np <= nthr ? nthr / np : 1;
   for (int p0 = 0; p0 < np; p0 += nthr / nsplit) {
     const int p = p0 + t % (nthr / nsplit), s = t / (nthr / nsplit);
-    real g = 0, g2 = 0;
+    real g = 0;
     if (p < np && s < nsplit) {
       const int m = B + p / b, n = B + p % b;
+      real acc[C];  // independent partial sums: the loads of C terms in flight
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = 0;
       int nu = s;
-      for (; nu + nsplit < K; nu += 2 * nsplit) {  // two independent chains
-        const int ua = coef_u[nu], ub = coef_u[nu + nsplit];
-        const int qa = ((((ua >> logF) * m + (ua & (F - 1)) * n) & (F - 1)) << tshift);
-        const int qb = ((((ub >> logF) * m + (ub & (F - 1)) * n) & (F - 1)) << tshift);
-        const real2 da = coef_d[nu], ea = tw[qa], db = coef_d[nu + nsplit], eb = tw[qb];
-        g += da.x * ea.x - da.y * ea.y;
-        g2 += db.x * eb.x - db.y * eb.y;
+      for (; nu + (C - 1) * nsplit < K; nu += C * nsplit) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int u = coef_u[nu + c * nsplit];
+          const int q = ((((u >> logF) * m + (u & (F - 1)) * n) & (F - 1)) << tshift);
+          const real2 d = coef_d[nu + c * nsplit], e = tw[q];
+          acc[c] += d.x * e.x - d.y * e.y;
+        }
       }
-      for (; nu < K; nu += nsplit) {
+      for (int c = 0; nu < K; nu += nsplit, ++c) {
         const int u = coef_u[nu];
         const int q = ((((u >> logF) * m + (u & (F - 1)) * n) & (F - 1)) << tshift);
         const real2 d = coef_d[nu], e = tw[q];
-        g += d.x * e.x - d.y * e.y;
+        acc[0] += d.x * e.x - d.y * e.y;
       }
-      g += g2;
+#pragma unroll
+      for (int c = 0; c < C; ++c) g += acc[c];
     }
     red[t] = g;
     bar<CTA>();
@@ -360,6 +365,23 @@ __device__ __forceinline__ void eval_and_write(const TileDev& T, const JobDev& J
     }
     bar<CTA>();
   }
+}
+
+// F = 32 (one warp per block): inline, two partial sums.
+template <bool CTA, typename real, typename real2>
+__device__ __forceinline__ void eval_and_write(const TileDev& T, const JobDev& J, real* val, int I, int Jb,
+                                               const int* coef_u, const real2* coef_d, const real2* tw,
+                                               real* red, int t, int nthr) {
+  eval_body<CTA, 2, real, real2>(T, J, val, I, Jb, coef_u, coef_d, tw, red, t, nthr);
+}
+
+// CTA-wide executors: eight partial sums in a call of its own, so the
+// evaluation's registers do not shape the allocation of the iteration loop.
+template <bool CTA, typename real, typename real2>
+__device__ __noinline__ void eval_and_write_call(const TileDev& T, const JobDev& J, real* val, int I,
+                                                 int Jb, const int* coef_u, const real2* coef_d,
+                                                 const real2* tw, real* red, int t, int nthr) {
+  eval_body<CTA, 8, real, real2>(T, J, val, I, Jb, coef_u, coef_d, tw, red, t, nthr);
 }
 
 __device__ __forceinline__ void debug_record(const ExecArgs& a, int cls, int id, const TileDev& T,
@@ -1185,7 +1207,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   __syncthreads();
   if (a.dbg_useq)
     for (int k = t; k < K; k += NT) debug_useq(a, CLS_F32_64, id, k, sm.coef_u[k]);
-  eval_and_write<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
+  eval_and_write_call<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
                                       NT);
 }
 
@@ -1334,7 +1356,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
   __syncthreads();
   if (a.dbg_useq)
     for (int k = t; k < K; k += NT) debug_useq(a, CLS_F32_64, id, k, sm.coef_u[k]);
-  eval_and_write<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
+  eval_and_write_call<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
                                       NT);
 }
 
@@ -1526,7 +1548,7 @@ __device__ __forceinline__ void item_f64(const ExecArgs& a, int id, CtaSmemD& sm
     }
     __syncthreads();
   }
-  eval_and_write<true, double, double2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
+  eval_and_write_call<true, double, double2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
                                         NT64);
 }
 
