@@ -66,6 +66,7 @@ def parse():
                     help="measured requests of the serving leg (0 = skip)")
     ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 6, 8])
     ap.add_argument("--f32-layout", type=int, default=0, choices=[0, 1, 2, 3])
+    ap.add_argument("--no-tma", action="store_true", help="stage supports with plain loads")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--study", default=None, choices=[None, "overlap", "tiling"],
                     help="run a study instead of the benchmark (one JSON line per result)")
@@ -402,6 +403,8 @@ def main():
         ctx.set_option(fse.OPT_F64_WARPS, args.f64_warps)
     if args.f32_layout:
         ctx.set_option(fse.OPT_F32_LAYOUT, args.f32_layout)
+    if args.no_tma:
+        ctx.set_option(fse.OPT_TMA_STAGING, 0)
     if args.ctas_per_sm:
         ctx.set_option(fse.OPT_CTAS_PER_SM, args.ctas_per_sm)
     keep, cjobs, pix = [], [], 0
@@ -518,7 +521,7 @@ def main():
     if rank == 0:
         cfg = describe(args.workload, jobs)
         cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                    "exec_mode": args.mode, "autotune": tuned, "l2": "flushed between steps (256 MB write)",
+                    "exec_mode": args.mode, "staging": "loads" if args.no_tma else "tma", "autotune": tuned, "l2": "flushed between steps (256 MB write)",
                     "lost_blocks_per_step": blocks, "core_lost_blocks_per_step": core_blocks,
                     "bin_iterations_per_step": bins})
         line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,

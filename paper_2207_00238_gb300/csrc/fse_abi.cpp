@@ -165,21 +165,23 @@ int enqueue_host(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st,
     int rc = check_job(jobs[i], i);
     if (rc) return rc;
     const size_t px = (size_t)jobs[i].W * jobs[i].H;
-    dj[i].image = (const uint8_t*)(c->arena + take(px));
-    dj[i].mask = (const uint8_t*)(c->arena + take(px));
-    dj[i].out = (uint8_t*)(c->arena + take(px));
+    const int dp = (jobs[i].W + 15) & ~15;  // device row pitch: 16-byte rows for the TMA staging
+    const size_t dpx = (size_t)dp * jobs[i].H;
+    dj[i].image = (const uint8_t*)(c->arena + take(dpx));
+    dj[i].mask = (const uint8_t*)(c->arena + take(dpx));
+    dj[i].out = (uint8_t*)(c->arena + take(dpx));
     dj[i].out_f32 = jobs[i].out_f32 ? (float*)(c->arena + take(px * 4)) : nullptr;
     dj[i].out_f64 = jobs[i].out_f64 ? (double*)(c->arena + take(px * 8)) : nullptr;
-    dj[i].pitch = jobs[i].W;
+    dj[i].pitch = dp;
   }
   off = (off + 255) / 256 * 256;
   if (off >= c->arena_bytes) return fail(FSE_ENOMEM, "arena too small for the host path");
   for (int i = 0; i < n; ++i) {
     const fse_job_t& j = jobs[i];
-    cudaError_t e = cudaMemcpy2DAsync((void*)dj[i].image, j.W, j.image, j.pitch, j.W, j.H,
+    cudaError_t e = cudaMemcpy2DAsync((void*)dj[i].image, dj[i].pitch, j.image, j.pitch, j.W, j.H,
                                       cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync((void*)dj[i].mask, j.W, j.mask, j.pitch, j.W, j.H,
+      e = cudaMemcpy2DAsync((void*)dj[i].mask, dj[i].pitch, j.mask, j.pitch, j.W, j.H,
                             cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
   }
@@ -187,7 +189,7 @@ int enqueue_host(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st,
   if (rc) return rc;
   for (int i = 0; i < n; ++i) {
     const fse_job_t& j = jobs[i];
-    cudaError_t e = cudaMemcpy2DAsync(j.out, j.pitch, dj[i].out, j.W, j.W, j.H,
+    cudaError_t e = cudaMemcpy2DAsync(j.out, j.pitch, dj[i].out, dj[i].pitch, j.W, j.H,
                                       cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && j.out_f32)
       e = cudaMemcpyAsync(j.out_f32, dj[i].out_f32, sizeof(float) * j.W * j.H,
@@ -210,7 +212,10 @@ size_t job_device_bytes(const fse_job_t& j) {
   const size_t ext_px = (size_t)(px * std::min(grow, (double)std::max(p.n_tiles, 1)) + 1);
   const size_t blocks = ext_px / ((size_t)p.block * p.block) + 4 * (size_t)p.n_tiles * (j.W + j.H) / p.block + 16;
   const size_t vbytes = p.precision == 64 ? 8 : 4;
-  return px * 3 + (j.out_f32 ? 4 * px : 0) + (j.out_f64 ? 8 * px : 0) + ext_px * vbytes +
+  const size_t dpx = (size_t)((j.W + 15) & ~15) * j.H;         // 16-byte device rows
+  const size_t vpad = (size_t)std::max(p.n_tiles, 1) * 3 * (j.H + 2 * (size_t)p.overlap) * vbytes;
+  const size_t maps = 128 * (2 + (size_t)std::max(p.n_tiles, 1)) + 256;  // tensor maps
+  return dpx * 3 + (j.out_f32 ? 4 * px : 0) + (j.out_f64 ? 8 * px : 0) + ext_px * vbytes + vpad + maps +
          blocks * (4 + 8 + 4 + 4 + 4 * MAX_CLS) + (size_t)(p.block + 2 * p.border) * (p.block + 2 * p.border) * 12 +
          (1 << 16);
 }
@@ -257,6 +262,11 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       return FSE_OK;
     case FSE_OPT_DEBUG_CAPTURE:
       c->debug = value != 0;
+      return FSE_OK;
+    case FSE_OPT_TMA_STAGING:
+      if (value != 0 && value != 1) return fse::fail(FSE_EINVAL, "tma staging");
+      c->tma = (int)value;
+      c->graph_jobs.clear();
       return FSE_OK;
     case FSE_OPT_F32_LAYOUT: {
       if (value < 0 || value > 3) return fse::fail(FSE_EINVAL, "f32 layout");

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>          // CUtensorMap and its enums (types only; libcuda is not linked)
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 #include <cuda_runtime.h>
 
 #include "../../include/fse.h"
@@ -254,6 +256,39 @@ static int ensure_host_buf(Context* c, size_t bytes) {
 }
 
 // ---------------------------------------------------------------------------
+// TMA tensor maps for the support staging.  The driver's encoder is reached
+// through the runtime's entry-point query, so libcuda is not linked.
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// 2-D tiled map: W x H elements of `esize` bytes, row stride `stride` bytes,
+// box bw x bh.  Out-of-range elements of a box read as zero.
+static bool encode_map(CUtensorMap* m, const void* base, bool f32, int W, int H, size_t stride, int bw,
+                       int bh) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+             const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
 // planning: tables for the device and the arena layout of one call
 // ---------------------------------------------------------------------------
 struct Plan {
@@ -262,6 +297,7 @@ struct Plan {
   std::vector<float> wf;
   std::vector<double> wd;
   std::vector<size_t> w_off;  // per job offset into wf / wd
+  std::vector<CUtensorMap> maps;  // per job: mask, image; then per tile: value plane
   int64_t total_blocks = 0;
   int64_t cap[MAX_CLS] = {0, 0, 0};
   int64_t val_f = 0, val_d = 0;  // elements
@@ -270,8 +306,8 @@ struct Plan {
   int64_t pixels = 0;
   // arena offsets (bytes)
   size_t o_jobs, o_tiles, o_wf, o_wd, o_map, o_items[MAX_CLS], o_cnt[MAX_CLS], o_slots[MAX_CLS],
-      o_valf, o_vald, o_q, o_level, o_dbg_rec, o_dbg_useq, upload_bytes, ff_begin, ff_end, zero_begin,
-      zero_end, total;
+      o_valf, o_vald, o_q, o_level, o_dbg_rec, o_dbg_useq, o_tmap, upload_bytes, ff_begin, ff_end,
+      zero_begin, zero_end, total;
 };
 
 static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena_offset, Plan& P) {
@@ -311,6 +347,16 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
     J.rho_f = (float)p.rho;
     J.delta_f = (float)p.delta;
     J.gamma_f = (float)p.gamma;
+    // TMA staging (F = 32 class): 16-byte aligned image and mask with a
+    // 16-byte multiple row stride (the encoder's rules); the maps are filled
+    // in once the arena layout is known
+    J.bw = (J.S + 15 + 15) & ~15;
+    J.bv = (J.S + 3 + 3) & ~3;
+    J.tma = c->tma && J.cls == CLS_F32_32 && ((uintptr_t)j.image & 15) == 0 && ((uintptr_t)j.mask & 15) == 0 &&
+            (j.pitch & 15) == 0 && J.bw <= 256 && J.S <= 256 && tmap_encoder() != nullptr;
+    J.tm_mask = nullptr;
+    J.tm_image = nullptr;
+    J.pad_ = 0;
     // rho^dist about the block centre, dist from (B + (b-1)/2, B + (b-1)/2)
     P.w_off[i] = P.wf.size();
     const double mc = p.border + (p.block - 1) / 2.0;
@@ -331,6 +377,9 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
       T.nbx = (T.ew + J.b - 1) / J.b;
       T.nby = (T.eh + J.b - 1) / J.b;
       T.cls = J.cls;
+      T.vp = J.cls == CLS_F32_32 ? (T.ew + 3) & ~3 : T.ew;  // 16-byte rows for the TMA
+      T.pad_ = 0;
+      T.tm_val = nullptr;
       T.map_off = P.total_blocks;
       const int64_t nb = (int64_t)T.nbx * T.nby;
       P.total_blocks += nb;
@@ -338,10 +387,10 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
       P.max_tile_blocks = (int)std::max<int64_t>(P.max_tile_blocks, nb);
       if (J.cls == CLS_F64) {
         T.val_off = P.val_d;
-        P.val_d += (int64_t)T.ew * T.eh;
+        P.val_d += (int64_t)T.vp * T.eh;
       } else {
         T.val_off = P.val_f;
-        P.val_f += (int64_t)T.ew * T.eh;
+        P.val_f += (int64_t)T.vp * T.eh;
       }
       P.tiles.push_back(T);
     }
@@ -355,6 +404,7 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
   P.o_tiles = take(sizeof(TileDev) * P.tiles.size());
   P.o_wf = take(sizeof(float) * P.wf.size());
   P.o_wd = take(sizeof(double) * P.wd.size());
+  P.o_tmap = take(sizeof(CUtensorMap) * (2 * (size_t)n + P.tiles.size()));
   P.upload_bytes = o - P.o_jobs;
   P.o_map = take(sizeof(int32_t) * P.total_blocks);
   for (int k = 0; k < MAX_CLS; ++k) {
@@ -383,6 +433,26 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
   for (int i = 0; i < n; ++i) {
     P.jobs[i].wiso_f = reinterpret_cast<const float*>(c->arena + P.o_wf) + P.w_off[i];
     P.jobs[i].wiso_d = reinterpret_cast<const double*>(c->arena + P.o_wd) + P.w_off[i];
+  }
+  // tensor maps: device copies land at o_tmap with the rest of the upload
+  P.maps.assign(2 * (size_t)n + P.tiles.size(), CUtensorMap{});
+  const CUtensorMap* dmaps = reinterpret_cast<const CUtensorMap*>(c->arena + P.o_tmap);
+  for (int i = 0; i < n; ++i) {
+    JobDev& J = P.jobs[i];
+    if (!J.tma) continue;
+    const bool ok = encode_map(&P.maps[2 * i], J.mask, false, J.W, J.H, (size_t)J.pitch, J.bw, J.S) &&
+                    encode_map(&P.maps[2 * i + 1], J.image, false, J.W, J.H, (size_t)J.pitch, J.bw, J.S);
+    J.tma = ok;
+    J.tm_mask = ok ? dmaps + 2 * i : nullptr;
+    J.tm_image = ok ? dmaps + 2 * i + 1 : nullptr;
+  }
+  for (size_t t = 0; t < P.tiles.size(); ++t) {
+    TileDev& T = P.tiles[t];
+    const JobDev& J = P.jobs[T.job];
+    if (!J.tma) continue;
+    const float* plane = reinterpret_cast<const float*>(c->arena + P.o_valf) + T.val_off;
+    if (encode_map(&P.maps[2 * n + t], plane, true, T.ew, T.eh, sizeof(float) * (size_t)T.vp, J.bv, J.S))
+      T.tm_val = dmaps + 2 * n + t;
   }
   return FSE_OK;
 }
@@ -543,6 +613,7 @@ int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse
   memcpy(c->host_buf + (P.o_tiles - P.o_jobs), P.tiles.data(), sizeof(TileDev) * P.tiles.size());
   memcpy(c->host_buf + (P.o_wf - P.o_jobs), P.wf.data(), sizeof(float) * P.wf.size());
   memcpy(c->host_buf + (P.o_wd - P.o_jobs), P.wd.data(), sizeof(double) * P.wd.size());
+  memcpy(c->host_buf + (P.o_tmap - P.o_jobs), P.maps.data(), sizeof(CUtensorMap) * P.maps.size());
   const ExecArgs a = make_args(c, P);
   const bool timed = stats != nullptr;
   if (timed) FSE_CUDA(cudaEventRecord(c->ev0, st));

@@ -36,6 +36,13 @@ struct JobDev {
   double rho, delta, gamma;
   const float* wiso_f;   // S*S, rho^dist about the block centre
   const double* wiso_d;  // same in FP64
+  // TMA staging of the support (F = 32 class): tensor maps of the mask and the
+  // image (u8, W x H, row stride pitch) in device memory, or null; box widths
+  // bw = roundup16(S + 15) (u8) and bv = roundup4(S + 3) (value plane, f32),
+  // both S rows high
+  const void* tm_mask;
+  const void* tm_image;
+  int32_t tma, bw, bv, pad_;
 };
 
 struct TileDev {
@@ -46,6 +53,9 @@ struct TileDev {
   int32_t cls;
   int64_t map_off;  // first block of this tile in the block map
   int64_t val_off;  // first pixel of this tile's value plane (elements)
+  const void* tm_val;  // tensor map of the value plane (f32, ew x eh, row stride vp), or null
+  int32_t vp;          // row pitch of the value plane (elements): ew, rounded up to 4 for F = 32
+  int32_t pad_;
 };
 
 // Per-class ready queue: an item is pushed once every block it depends on is

@@ -170,7 +170,7 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
   const int n = t & (F - 1), m0 = t / F, mstep = nthr / F;
   const int tx = ox + n;
   const bool col_in = n < S && tx >= 0 && tx < T.ew;
-  const int ew = T.ew, eh = T.eh;
+  const int eh = T.eh, vp = F == 32 ? T.vp : T.ew;  // F = 64 value planes are unpadded
   const size_t pitch = J.pitch, g0 = (size_t)T.ey * pitch + T.ex;
   const uint8_t* mask = J.mask;
   const uint8_t* image = J.image;
@@ -185,7 +185,7 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
       const int m = mb + u * mstep, ty = oy + m;
       in[u] = col_in && m < S && ty >= 0 && ty < eh;
       const size_t gi = in[u] ? g0 + (size_t)ty * pitch + tx : g0;
-      const size_t vi = in[u] ? (size_t)ty * ew + tx : 0;
+      const size_t vi = in[u] ? (size_t)ty * vp + tx : 0;
       wi[u] = __ldg(wiso + (m < S ? m * S + n : n));
       mk[u] = __ldg(mask + gi);
       px[u] = __ldg(image + gi);
@@ -210,6 +210,124 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
       z.y = zr;
       zbuf[swz<F>(m, n)] = z;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA support staging (F = 32 executor, where twelve warps per SM share the
+// load/store queue with the iteration loops).  One thread issues three tensor
+// copies per block (the mask and image boxes from the job's maps, the
+// value-plane box from the tile's map) that complete on an mbarrier; every x
+// coordinate is rounded down to a 16-byte multiple and the boxes are wide
+// enough to cover the support from there (bw = roundup16(S + 15) bytes,
+// bv = roundup4(S + 3) floats), so no copy starts off a 16-byte boundary.
+// Elements outside the image or the tile read as zero and are masked by the
+// same in-tile test as the plain loads.  The wait is bounded by the context's
+// wall-clock limit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Support bytes the three boxes need in shared memory (each box 128-byte aligned).
+__device__ __forceinline__ int tma_stage_bytes(const JobDev& J) {
+  return 2 * ((J.S * J.bw + 127) & ~127) + J.S * J.bv * 4;
+}
+
+// Issues the copies (leader thread only) after ordering earlier shared-memory
+// accesses of the buffer before the asynchronous writes.
+__device__ __forceinline__ void tma_issue_support(const TileDev& T, const JobDev& J, int I, int Jb,
+                                                  unsigned char* sbuf, uint64_t* mbar) {
+  const int S = J.S;
+  const int oy = I * J.b - J.B, ox = Jb * J.b - J.B;
+  const int x0 = (T.ex + ox) & ~15, vx0 = ox & ~3, gy = T.ey + oy;
+  const int sz8 = (S * J.bw + 127) & ~127;
+  const uint32_t mb = smem_u32(mbar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+               "r"((uint32_t)(2 * S * J.bw + S * J.bv * 4))
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(sbuf)),
+      "l"(J.tm_mask), "r"(x0), "r"(gy), "r"(mb)
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(sbuf + sz8)),
+      "l"(J.tm_image), "r"(x0), "r"(gy), "r"(mb)
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(sbuf + 2 * sz8)),
+      "l"(T.tm_val), "r"(vx0), "r"(oy), "r"(mb)
+      : "memory");
+}
+
+// Waits for phase `parity` of the mbarrier; false when the wall-clock limit passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int64_t timeout_ns) {
+  const uint32_t mb = smem_u32(mbar);
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(done)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 63) == 63 && (int64_t)(global_ns() - t0) > timeout_ns) return false;
+  }
+}
+
+// Whether this block can be staged by TMA into `sbuf` (bytes available).
+__device__ __forceinline__ bool tma_usable(const TileDev& T, const JobDev& J, const unsigned char* sbuf,
+                                           int bytes) {
+  return J.tma && T.tm_val != nullptr && sbuf != nullptr && (smem_u32(sbuf) & 127) == 0 &&
+         tma_stage_bytes(J) <= bytes;
+}
+
+// z(m, n) = (w, w*r) from the landed boxes; same thread mapping and the same
+// arithmetic as stage_support.
+template <int F>
+__device__ __forceinline__ void stage_from_boxes(const TileDev& T, const JobDev& J, int I, int Jb,
+                                                 float2* zbuf, const unsigned char* sbuf, int t, int nthr) {
+  const int S = J.S, bw = J.bw, bv = J.bv;
+  const int oy = I * J.b - J.B, ox = Jb * J.b - J.B;
+  const int gx = T.ex + ox;
+  const int dx8 = gx - (gx & ~15), dxv = ox - (ox & ~3);
+  const int sz8 = (S * bw + 127) & ~127;
+  const unsigned char* smask = sbuf;
+  const unsigned char* simg = sbuf + sz8;
+  const float* sval = reinterpret_cast<const float*>(sbuf + 2 * sz8);
+  const float* wiso = J.wiso_f;
+  const float delta = J.delta_f;
+  const bool use_done = J.order != ORDER_INDEPENDENT;
+  const int n = t & (F - 1), m0 = t / F, mstep = nthr / F;
+  if (n >= S) return;
+  const int tx = ox + n;
+  const bool col_in = tx >= 0 && tx < T.ew;
+  for (int m = m0; m < S; m += mstep) {
+    const int ty = oy + m;
+    float wv = 0.f, zr = 0.f;
+    if (col_in && ty >= 0 && ty < T.eh) {
+      const float wi = __ldg(wiso + m * S + n);
+      const int mk = smask[m * bw + dx8 + n];
+      if (mk == 0) {
+        wv = wi;
+        zr = wi * (float)simg[m * bw + dx8 + n];
+      } else if (use_done) {
+        const float v = sval[m * bv + dxv + n];
+        if (!isnan(v)) {
+          wv = delta * wi;
+          zr = wv * v;
+        }
+      }
+    }
+    zbuf[swz<F>(m, n)] = make_float2(wv, zr);
   }
 }
 
@@ -354,7 +472,7 @@ __device__ __forceinline__ void eval_body(const TileDev& T, const JobDev& J, rea
         const int gy = T.ey + ty, gx = T.ex + tx;
         const size_t gi = (size_t)gy * J.pitch + gx;
         if (__ldg(J.mask + gi) != 0) {
-          val[(size_t)ty * T.ew + tx] = g;
+          val[(size_t)ty * (CTA ? T.ew : T.vp) + tx] = g;  // CTA-wide executors: unpadded planes
           if (gx >= T.x && gx < T.x + T.w && gy >= T.y && gy < T.y + T.h) {
             J.out[gi] = to_u8(g);
             if (J.out_f32) J.out_f32[(size_t)gy * J.W + gx] = (float)g;
@@ -552,11 +670,14 @@ __device__ __forceinline__ void static_for(Fn&& f) {
 // shared memory with its 32 rows stored twice, so W(k - u) for row j is at a
 // per-iteration base plus the compile-time offset j * 32.
 // ===========================================================================
-struct alignas(16) WarpSmem32 {
-  float2 Wd[64 * 32];     // rows 0..63: W rows (r mod 32); 32..63 double as FFT buffer
+struct alignas(128) WarpSmem32 {
+  float2 Wd[64 * 32];     // rows 0..63: W rows (r mod 32); 32..63 double as FFT buffer,
+                          // 0..31 take the TMA support boxes during staging
   float2 coef_d[KMAX];
   int32_t coef_u[KMAX];
   float red[32];
+  uint64_t mbar;          // completion of the TMA staging copies
+  uint32_t tma_ph;        // stagings done (phase parity)
   TileDev T;              // descriptors of the current block's tile and job
   JobDev J;
 };
@@ -568,7 +689,7 @@ constexpr size_t SMEM32 = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32);
 // FFTs into registers: x[k1] = Z(k1, lane).
 template <class WS>
 __device__ __forceinline__ void stage_fft32(const ExecArgs& a, int id, WS& sm, float2* zbuf, int lane,
-                                            float2 (&x)[32]) {
+                                            float2 (&x)[32], unsigned char* sbuf, int sbytes) {
   const ClassArgs& C = a.c[CLS_F32_32];
   const int2 it = C.items[id];
   copy_desc(&sm.T, a.tiles + it.x, lane, 32);
@@ -581,7 +702,19 @@ __device__ __forceinline__ void stage_fft32(const ExecArgs& a, int id, WS& sm, f
   const int S = J.S;
   float* val = a.val_f + T.val_off;
   if (lane == 0) debug_record(a, CLS_F32_32, id, T, it.x, I, Jb);
-  stage_support<32, float, float2>(T, J, val, I, Jb, zbuf, lane, 32);
+  if (tma_usable(T, J, sbuf, sbytes)) {
+    const uint32_t ph = sm.tma_ph;
+    if (lane == 0) tma_issue_support(T, J, I, Jb, sbuf, &sm.mbar);
+    if (!mbar_wait(&sm.mbar, ph & 1, a.timeout_ns)) {
+      if (lane == 0) atomicOr(&C.q->error, ERR_TIMEOUT);
+      mbar_wait(&sm.mbar, ph & 1, a.timeout_ns);  // the copies in flight, bounded again
+    }
+    stage_from_boxes<32>(T, J, I, Jb, zbuf, sbuf, lane, 32);
+    __syncwarp();
+    if (lane == 0) sm.tma_ph = ph + 1;
+  } else {
+    stage_support<32, float, float2>(T, J, val, I, Jb, zbuf, lane, 32);
+  }
   __syncwarp();
   // row FFTs: lane m transforms support row m
   if (lane < S) {
@@ -603,8 +736,8 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
                             int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
   float2 x[32];
-  // stage -> rows 32..63 (swizzled F x F buffer)
-  stage_fft32(a, id, sm, sm.Wd + 32 * 32, lane, x);
+  // stage -> rows 32..63 (swizzled F x F buffer); TMA boxes in rows 0..31
+  stage_fft32(a, id, sm, sm.Wd + 32 * 32, lane, x, reinterpret_cast<unsigned char*>(sm.Wd), 8192);
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -704,11 +837,13 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
 // lower lane holds the lower row, then the lower column: the lowest lane is
 // the lowest flat index.
 // ---------------------------------------------------------------------------
-struct alignas(16) WarpSmem32P {
-  float4 Wt[35 * 32];
+struct alignas(128) WarpSmem32P {
+  float4 Wt[35 * 32];  // rows 16..34 take the TMA support boxes during staging
   float2 coef_d[KMAX];
   int32_t coef_u[KMAX];
   float red[32];
+  uint64_t mbar;
+  uint32_t tma_ph;
   TileDev T;
   JobDev J;
 };
@@ -719,7 +854,7 @@ __device__ __forceinline__ void item_f32_32p(const ExecArgs& a, int id, WarpSmem
   float2* zbuf = reinterpret_cast<float2*>(sm.Wt);
   float4* Wt = sm.Wt;
   float2 x[32];
-  stage_fft32(a, id, sm, zbuf, lane, x);
+  stage_fft32(a, id, sm, zbuf, lane, x, reinterpret_cast<unsigned char*>(sm.Wt) + 8192, 35 * 32 * 16 - 8192);
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -841,11 +976,14 @@ constexpr size_t SMEM32P = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32P);
 // warp) and the table overlays the FFT buffer.  Same arithmetic and keys as
 // the column layout; more warps fit on an SM.
 // ---------------------------------------------------------------------------
-struct alignas(16) WarpSmem32R {
+struct alignas(128) WarpSmem32R {
   float2 Wd[35 * 32];  // W rows 0..31, rows 32..34 repeat rows 0..2; rows 0..31 double as FFT buffer
   float2 coef_d[KMAX];
   int32_t coef_u[KMAX];
   float red[32];
+  unsigned char stage_pad[3712];  // bytes 8192..15871 from Wd take the TMA support boxes
+  uint64_t mbar;
+  uint32_t tma_ph;
   TileDev T;
   JobDev J;
 };
@@ -854,7 +992,7 @@ __device__ __forceinline__ void item_f32_32r(const ExecArgs& a, int id, WarpSmem
                                              int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
   float2 x[32];
-  stage_fft32(a, id, sm, sm.Wd, lane, x);
+  stage_fft32(a, id, sm, sm.Wd, lane, x, reinterpret_cast<unsigned char*>(sm.Wd) + 8192, 7680);
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -956,13 +1094,18 @@ __device__ __forceinline__ void run_item32(const ExecArgs& a, int id, WS& sm, co
 template <class WS>
 __global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32R>::value ? 6 : 5)
     k_exec_f32_32(const __grid_constant__ ExecArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);
-  WS* wsm = reinterpret_cast<WS*>(smem_raw + 64 * sizeof(float2));
+  extern __shared__ __align__(128) unsigned char smem32_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem32_raw);
+  WS* wsm = reinterpret_cast<WS*>(smem32_raw + 64 * sizeof(float2));
   for (int q = threadIdx.x; q < 64; q += blockDim.x) tw[q] = make_float2(c_twf[q].x, -c_twf[q].y);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WS& sm = wsm[warp];
+  if (lane == 0) {
+    mbar_init(&sm.mbar);
+    sm.tma_ph = 0;
+  }
+  __syncwarp();
   const ClassArgs& C = a.c[CLS_F32_32];
   if (a.single_item >= 0) {
     if (blockIdx.x == 0 && warp == 0) run_item32(a, a.single_item, sm, tw, lane);

@@ -134,6 +134,10 @@ int run(const fse_job_t* jobs, int32_t n, cudaStream_t st) {
     J.rho_f = (float)p.rho;
     J.delta_f = (float)p.delta;
     J.gamma_f = (float)p.gamma;
+    J.tm_mask = nullptr;  // no tensor maps here: the support is staged with plain loads
+    J.tm_image = nullptr;
+    J.tma = 0;
+    J.bw = J.bv = 0;
     const double mc = p.border + (p.block - 1) / 2.0;
     w_off[i] = nw;  // the table's pointers are set once the layout is known
     for (int m = 0; m < J.S; ++m)
@@ -153,6 +157,9 @@ int run(const fse_job_t* jobs, int32_t n, cudaStream_t st) {
       T.nbx = (T.ew + J.b - 1) / J.b;
       T.nby = (T.eh + J.b - 1) / J.b;
       T.cls = J.cls;
+      T.vp = T.ew;
+      T.pad_ = 0;
+      T.tm_val = nullptr;
       T.map_off = total_blocks;
       const int64_t nb = (int64_t)T.nbx * T.nby;
       total_blocks += nb;

@@ -100,6 +100,27 @@ def test_fp32_f32_executor_layouts(ctx, oracle_lib, layout, case):
     _fp32_check(oracle_lib, job, got[0])
 
 
+@pytest.mark.parametrize("layout64,layout32", [(6, 3), (4, 1), (5, 2)])
+def test_tma_staging_matches_plain_loads(ctx, layout64, layout32):
+    """Support staging by TMA tensor copies hands the executors the same
+    weights and values as plain loads: identical bytes and model values."""
+    jobs = [CASES["plain_64"](), CASES["defects_small"](), _small_tiled()]
+    res = {}
+    for tma in (0, 1):
+        ctx.set_option(fse.OPT_TMA_STAGING, tma)
+        ctx.set_option(fse.OPT_F64_WARPS, layout64)
+        ctx.set_option(fse.OPT_F32_LAYOUT, layout32)
+        try:
+            res[tma], _ = run_gpu(ctx, jobs)
+        finally:
+            ctx.set_option(fse.OPT_TMA_STAGING, 1)
+            ctx.set_option(fse.OPT_F64_WARPS, 0)
+            ctx.set_option(fse.OPT_F32_LAYOUT, 0)
+    for a, b in zip(res[0], res[1]):
+        assert (a["out"] == b["out"]).all()
+        np.testing.assert_array_equal(a["g"], b["g"])
+
+
 def test_f32_run_layout_matches_column_layout(ctx):
     """The row-run layout of the F = 32 executor does the column layout's
     arithmetic in the same order: identical bytes and model values."""
