@@ -194,7 +194,8 @@ def run_reference(args, rank, world):
         return
     jobs = workload(args.workload)
     job = jobs[0]
-    per_step = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    # ~150 s of oracle work for the whole run, whatever K and W (at least 16 blocks a step)
+    per_step = max(0.05, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
     _, n, _, cores = oracle_blocks_per_s(job, per_step)
     for _ in range(args.warmup):
         oracle_blocks_per_s(job, per_step, max_blocks=n)
