@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 6, 8])
     ap.add_argument("--f32-layout", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--no-tma", action="store_true", help="stage supports with plain loads")
+    ap.add_argument("--no-graph", action="store_true", help="time direct launches instead of graph replay")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--study", default=None, choices=[None, "overlap", "tiling"],
                     help="run a study instead of the benchmark (one JSON line per result)")
@@ -429,10 +430,21 @@ def main():
     blocks, core_blocks, bins = st["lost_blocks"], st["core_lost_blocks"], st["bin_iterations"]
     launches_per_step = st["launches"]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
-        ctx.extrapolate(cjobs, stream=sptr, stats=False)
+    # the iteration kernels' durations: a pass of their own without graph
+    # replay (kernel-timing events are not captured into the graph)
     ctx.set_option(fse.OPT_KERNEL_TIMING, 1)
     ctx.kernel_times()
+    for i in range(max(3, min(args.steps, 50))):
+        flush.fill_(float(i))
+        ctx.extrapolate(cjobs, stream=sptr, stats=False)
+    torch.cuda.synchronize()
+    kern_ms = ctx.kernel_times()
+    ctx.set_option(fse.OPT_KERNEL_TIMING, 0)
+    # the timed steps replay the call's CUDA graph (captured on the first call)
+    if not args.no_graph:
+        ctx.set_option(fse.OPT_USE_GRAPH, 1)
+    for _ in range(args.warmup):
+        ctx.extrapolate(cjobs, stream=sptr, stats=False)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if dist:
@@ -452,8 +464,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    kern_ms = ctx.kernel_times()
-    ctx.set_option(fse.OPT_KERNEL_TIMING, 0)
+    ctx.set_option(fse.OPT_USE_GRAPH, 0)
     total_s = max_over_ranks(sum(step_ms) / 1000.0, dist, dev)
     value = whole_job_rate(blocks, world, args.steps, total_s)
     mpix = world * pix * args.steps / total_s / 1e6
@@ -532,7 +543,7 @@ def main():
     if rank == 0:
         cfg = describe(args.workload, jobs)
         cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                    "exec_mode": args.mode, "staging": "loads" if args.no_tma else "tma", "autotune": tuned, "l2": "flushed between steps (256 MB write)",
+                    "exec_mode": args.mode, "staging": "loads" if args.no_tma else "tma", "launch": "direct" if args.no_graph else "cuda graph replay", "autotune": tuned, "l2": "flushed between steps (256 MB write)",
                     "lost_blocks_per_step": blocks, "core_lost_blocks_per_step": core_blocks,
                     "bin_iterations_per_step": bins})
         line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,
