@@ -72,3 +72,26 @@ def test_last_error_is_a_string(lib):
     with pytest.raises(fse.FseError):
         fse.plan_tiles(0, 0, 0, 0)
     assert "invalid" in lib.fse_last_error().decode()
+
+
+def test_binding_constants_match_header():
+    """The binding's status codes, option keys and enum values equal the
+    header's #defines (the two are maintained side by side)."""
+    import re
+    import paper_2207_00238_gb300 as fse
+    hdr = open(os.path.join(ROOT, "include", "fse.h")).read()
+    defs = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"#define FSE_(\w+)\s+\(?(-?\d+)\)?", hdr)}
+    for name in ["OK", "EINVAL", "EDEGENERATE", "ENOMEM", "EBUSY", "ETIMEOUT", "ECUDA", "ENOTFOUND",
+                 "ECANCELLED"]:
+        assert getattr(fse, name) == defs[name], name
+    for key, val in fse.ORDER.items():
+        assert val == defs["ORDER_" + key.upper()], key
+    for key, val in fse.TILING.items():
+        assert val == defs["TILING_" + key.upper()], key
+    for key, val in fse.EXEC.items():
+        assert val == defs["EXEC_" + key.upper()], key
+    opts = [n for n in dir(fse) if n.startswith("OPT_")]
+    assert len(opts) == len([d for d in defs if d.startswith("OPT_")])
+    for n in opts:
+        assert getattr(fse, n) == defs[n], n
