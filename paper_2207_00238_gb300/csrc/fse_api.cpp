@@ -389,6 +389,7 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
         T.val_off = P.val_d;
         P.val_d += (int64_t)T.vp * T.eh;
       } else {
+        if (J.cls == CLS_F32_32) P.val_f = (P.val_f + 3) & ~(int64_t)3;  // 16-byte plane base for the TMA
         T.val_off = P.val_f;
         P.val_f += (int64_t)T.vp * T.eh;
       }
