@@ -121,6 +121,28 @@ def test_tma_staging_matches_plain_loads(ctx, layout64, layout32):
         np.testing.assert_array_equal(a["g"], b["g"])
 
 
+@pytest.mark.parametrize("layout32", [3, 2])
+def test_tma_staging_small_support(ctx, oracle_lib, layout32):
+    """A support smaller than the DFT (b=4, B=8: S=20 in F=32) narrows the TMA
+    boxes; TMA and plain loads agree bit for bit and meet the FP32 gate."""
+    rng = synth.Rng(synth.SEED_BASE + 41)
+    img = synth.image(96, 64, rng, structure=True)
+    mask, _ = synth.block_mask(96, 64, 4, 60, rng)
+    job = dict(image=img, mask=mask, params=synth.params(4, 8, 32, 60, n_tiles=2, overlap=12))
+    res = {}
+    for tma in (0, 1):
+        ctx.set_option(fse.OPT_TMA_STAGING, tma)
+        ctx.set_option(fse.OPT_F32_LAYOUT, layout32)
+        try:
+            res[tma], _ = run_gpu(ctx, [job])
+        finally:
+            ctx.set_option(fse.OPT_TMA_STAGING, 1)
+            ctx.set_option(fse.OPT_F32_LAYOUT, 0)
+    assert (res[0][0]["out"] == res[1][0]["out"]).all()
+    np.testing.assert_array_equal(res[0][0]["g"], res[1][0]["g"])
+    _fp32_check(oracle_lib, job, res[1][0])
+
+
 def test_f32_run_layout_matches_column_layout(ctx):
     """The row-run layout of the F = 32 executor does the column layout's
     arithmetic in the same order: identical bytes and model values."""
