@@ -543,7 +543,7 @@ def main():
     if rank == 0:
         cfg = describe(args.workload, jobs)
         cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                    "exec_mode": args.mode, "staging": "loads" if args.no_tma else "tma", "launch": "direct" if args.no_graph else "cuda graph replay", "autotune": tuned, "l2": "flushed between steps (256 MB write)",
+                    "exec_mode": args.mode, "staging": "loads" if args.no_tma else "tma where many F=32 blocks (auto)", "launch": "direct" if args.no_graph else "cuda graph replay", "autotune": tuned, "l2": "flushed between steps (256 MB write)",
                     "lost_blocks_per_step": blocks, "core_lost_blocks_per_step": core_blocks,
                     "bin_iterations_per_step": bins})
         line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,

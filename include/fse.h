@@ -165,11 +165,13 @@ void fse_context_destroy(fse_context_t* ctx);
                                    column per lane read in row runs (35-row W
                                    table, 6 blocks of 2 warps per SM); 0 =
                                    default (3)                                 */
-#define FSE_OPT_TMA_STAGING 9   /* 1 (default) = the F = 32 executor stages each
-                                   block's support with TMA tensor copies where
-                                   the job's image and mask are 16-byte aligned
-                                   with a 16-byte multiple row pitch; 0 = plain
-                                   loads (always so for F = 64 and FP64)       */
+#define FSE_OPT_TMA_STAGING 9   /* 1 = the F = 32 executor stages each block's
+                                   support with TMA tensor copies where the
+                                   job's image and mask are 16-byte aligned
+                                   with a 16-byte multiple row pitch; 2
+                                   (default) = the same when the call has at
+                                   least four F = 32 blocks per resident warp;
+                                   0 = plain loads (always so for F = 64, FP64) */
 #define FSE_OPT_KERNEL_TIMING 6 /* 1 = bracket the iteration kernels of every
                                    call with CUDA events (no synchronisation);
                                    read with fse_context_kernel_times         */

@@ -264,7 +264,7 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       c->debug = value != 0;
       return FSE_OK;
     case FSE_OPT_TMA_STAGING:
-      if (value != 0 && value != 1) return fse::fail(FSE_EINVAL, "tma staging");
+      if (value < 0 || value > 2) return fse::fail(FSE_EINVAL, "tma staging");
       c->tma = (int)value;
       c->graph_jobs.clear();
       return FSE_OK;

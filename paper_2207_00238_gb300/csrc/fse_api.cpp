@@ -398,6 +398,12 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
   }
   for (int k = 0; k < MAX_CLS; ++k)
     if (P.cap[k] >= (1ll << 31)) return fail(FSE_EINVAL, "too many blocks in one call");
+  // auto: the TMA copies take longer per block than plain loads but free the
+  // load/store queue, which pays only when many blocks share each SM, so they
+  // are used when the F = 32 class has at least four blocks per resident warp
+  if (c->tma == 2 &&
+      P.cap[CLS_F32_32] < 4ll * exec_grid(c, CLS_F32_32) * (exec_threads(CLS_F32_32) / 32))
+    for (JobDev& J : P.jobs) J.tma = 0;
   // arena layout (bytes from the arena base + arena_offset)
   size_t o = arena_offset;
   auto take = [&](size_t bytes) { size_t r = align_up(o, 256); o = r + bytes; return r; };

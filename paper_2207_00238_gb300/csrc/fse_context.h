@@ -27,7 +27,7 @@ struct fse_context {
   int use_graph = 0;
   int debug = 0;
   int kernel_timing = 0;
-  int tma = 1;  // stage supports with TMA where the job's buffers allow it
+  int tma = 2;  // TMA staging of F = 32 supports: 0 off, 1 where the buffers allow it, 2 auto
   int capturing = 0;
   std::vector<cudaEvent_t> tev;  // pairs: start, end of the iteration kernels
   size_t tev_used = 0;

@@ -113,7 +113,7 @@ def test_tma_staging_matches_plain_loads(ctx, layout64, layout32):
         try:
             res[tma], _ = run_gpu(ctx, jobs)
         finally:
-            ctx.set_option(fse.OPT_TMA_STAGING, 1)
+            ctx.set_option(fse.OPT_TMA_STAGING, 2)
             ctx.set_option(fse.OPT_F64_WARPS, 0)
             ctx.set_option(fse.OPT_F32_LAYOUT, 0)
     for a, b in zip(res[0], res[1]):
@@ -136,7 +136,7 @@ def test_tma_staging_small_support(ctx, oracle_lib, layout32):
         try:
             res[tma], _ = run_gpu(ctx, [job])
         finally:
-            ctx.set_option(fse.OPT_TMA_STAGING, 1)
+            ctx.set_option(fse.OPT_TMA_STAGING, 2)
             ctx.set_option(fse.OPT_F32_LAYOUT, 0)
     assert (res[0][0]["out"] == res[1][0]["out"]).all()
     np.testing.assert_array_equal(res[0][0]["g"], res[1][0]["g"])
