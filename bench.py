@@ -33,9 +33,8 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 SMEM_BYTES_PER_CLK_SM = 128  # shared-memory bandwidth per SM per clock
 BYTES_PER_BIN_ITER = 8       # the gathered complex FP32 W(k-u) value
 
-# DRAM bytes per launch of the dominant kernel from the committed ncu captures
-# (profiles/k_exec_f32_64_tiled_1024.md, profiles/k_exec_f32_32_defects_4k.md),
-# reported only while the kernel source is the one that was captured.
+# DRAM bytes per launch of the dominant kernel from an ncu capture of the same
+# workload, reported only while the kernel source is the one that was captured.
 CAPTURED_TRAFFIC = {"kernel_src_sha256_16": "036fbba36bddb834",
                     "tiled_1024": 8307200, "defects_4k": 53262336 + 2532608}
 

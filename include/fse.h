@@ -172,6 +172,11 @@ void fse_context_destroy(fse_context_t* ctx);
                                    (default) = the same when the call has at
                                    least four F = 32 blocks per resident warp;
                                    0 = plain loads (always so for F = 64, FP64) */
+#define FSE_OPT_DEBUG_TMA_STALL 10 /* test only: 1 = the TMA staging of F = 32
+                                   supports never signals completion, so its
+                                   bounded wait runs out: the call returns
+                                   FSE_ETIMEOUT and the context stays usable
+                                   (exercises the failure path, no fault)     */
 #define FSE_OPT_KERNEL_TIMING 6 /* 1 = bracket the iteration kernels of every
                                    call with CUDA events (no synchronisation);
                                    read with fse_context_kernel_times         */

@@ -291,6 +291,10 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       c->graph_jobs.clear();
       return FSE_OK;
     }
+    case FSE_OPT_DEBUG_TMA_STALL:
+      c->dbg_tma_stall = value != 0;
+      c->graph_jobs.clear();
+      return FSE_OK;
     case FSE_OPT_KERNEL_TIMING:
       c->kernel_timing = value != 0;
       c->tev_used = 0;

@@ -489,6 +489,7 @@ static ExecArgs make_args(Context* c, const Plan& P) {
     a.dbg_cap = (int32_t)std::max({P.cap[0], P.cap[1], P.cap[2]});
   }
   a.single_item = -1;
+  a.dbg_tma_stall = c->dbg_tma_stall;
   return a;
 }
 

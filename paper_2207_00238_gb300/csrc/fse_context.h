@@ -29,6 +29,7 @@ struct fse_context {
   int kernel_timing = 0;
   int tma = 2;  // TMA staging of F = 32 supports: 0 off, 1 where the buffers allow it, 2 auto
   int capturing = 0;
+  int dbg_tma_stall = 0;  // test only (FSE_OPT_DEBUG_TMA_STALL)
   std::vector<cudaEvent_t> tev;  // pairs: start, end of the iteration kernels
   size_t tev_used = 0;
   int occupancy[fse::MAX_CLS] = {1, 1, 1};

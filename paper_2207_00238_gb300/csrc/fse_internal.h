@@ -97,6 +97,7 @@ struct ExecArgs {
   int32_t level_mode;   // 0 = DAG, 1 = only items whose level == level
   int32_t level;
   int32_t single_item;  // >= 0: process exactly this item (per-block launch)
+  int32_t dbg_tma_stall;  // test only: TMA stagings never complete their mbarrier phase
   int32_t* level_of;    // per class item level (levels mode), class stride level_stride
   int64_t level_stride;
 };

@@ -4,9 +4,11 @@
 //   stage   : gather the S x S support (S = b + 2B) around the block from the
 //             8-bit image, the loss mask and the tile's value plane; weight
 //             w = rho^dist (known), delta*rho^dist (reconstructed), 0 (pending
-//             or outside the extended tile); z = w + i*w*r.
-//   DFT     : one packed complex F x F FFT of z (zero padded S -> F), split by
-//             Hermitian symmetry into W = DFT(w) and R_w = DFT(w*r).
+//             or outside the extended tile); rbar = sum(w r) / sum(w).
+//   DFT     : one packed complex F x F FFT of w + i*w*(r - rbar) (zero padded
+//             S -> F), split by Hermitian symmetry into W = DFT(w) and
+//             R' = DFT(w*(r - rbar)); R_w = rbar*W + R' (= DFT(w*r)).  FP64
+//             path: R_w = DFT(w*r) directly.
 //   iterate : K times: u = argmax_k |R_w(k)|^2; Delta = gamma R_w(u) / W(0);
 //             record (u, Delta); R_w(k) -= Delta * W(k - u) for every bin k.
 //   model   : g = Re sum Delta_nu exp(+2 pi i u_nu . x / F) at the block's
@@ -140,9 +142,10 @@ __device__ __forceinline__ uint8_t to_u8(double g) {
 }
 
 // ---------------------------------------------------------------------------
-// Support staging: z(m, n) = (w, w*r) for m, n < S into a swizzled F x F
-// buffer; element (m, n) lives at m*F + (n ^ (m & (F-1))) so that row-wise and
-// column-wise walks of a warp hit distinct banks.
+// Support staging: z(m, n) = (w, r) for m, n < S into a swizzled F x F buffer
+// (r = 0 where w = 0); element (m, n) lives at m*F + (n ^ (m & (F-1))) so that
+// row-wise and column-wise walks of a warp hit distinct banks.  The row FFTs
+// read (w, w (r - c)) from it, c the support's weighted mean (support_mean).
 // ---------------------------------------------------------------------------
 template <int F>
 __device__ __forceinline__ int swz(int m, int n) {
@@ -195,19 +198,19 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
     for (int u = 0; u < U; ++u) {
       const int m = mb + u * mstep;
       if (m >= S) break;
-      real wv = 0, zr = 0;
+      real wv = 0, rv = 0;
       if (in[u]) {
         if (mk[u] == 0) {
           wv = wi[u];
-          zr = wi[u] * (real)px[u];
+          rv = (real)px[u];
         } else if (use_done && !isnan(v[u])) {
           wv = delta * wi[u];
-          zr = wv * v[u];
+          rv = v[u];
         }
       }
       real2 z;
       z.x = wv;
-      z.y = zr;
+      z.y = rv;
       zbuf[swz<F>(m, n)] = z;
     }
   }
@@ -237,19 +240,27 @@ __device__ __forceinline__ int tma_stage_bytes(const JobDev& J) {
   return 2 * ((J.S * J.bw + 127) & ~127) + J.S * J.bv * 4;
 }
 
-// Issues the copies (leader thread only) after ordering earlier shared-memory
-// accesses of the buffer before the asynchronous writes.
+// Issues the copies (leader thread only).  The value plane was written with
+// ordinary stores by the warps that reconstructed earlier blocks and published
+// through the ready queue (release / acquire); the global proxy fence orders
+// what this thread has thereby observed before its asynchronous-proxy reads,
+// and the shared one orders earlier accesses of the buffer before the
+// asynchronous writes.  stall (test only): expect the bytes without arriving,
+// so the phase cannot complete until the waiter arrives itself.
 __device__ __forceinline__ void tma_issue_support(const TileDev& T, const JobDev& J, int I, int Jb,
-                                                  unsigned char* sbuf, uint64_t* mbar) {
+                                                  unsigned char* sbuf, uint64_t* mbar, bool stall) {
   const int S = J.S;
   const int oy = I * J.b - J.B, ox = Jb * J.b - J.B;
   const int x0 = (T.ex + ox) & ~15, vx0 = ox & ~3, gy = T.ey + oy;
   const int sz8 = (S * J.bw + 127) & ~127;
   const uint32_t mb = smem_u32(mbar);
+  const uint32_t bytes = (uint32_t)(2 * S * J.bw + S * J.bv * 4);
+  asm volatile("fence.proxy.async.global;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-               "r"((uint32_t)(2 * S * J.bw + S * J.bv * 4))
-               : "memory");
+  if (stall)
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+  else
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           smem_u32(sbuf)),
@@ -265,6 +276,11 @@ __device__ __forceinline__ void tma_issue_support(const TileDev& T, const JobDev
           smem_u32(sbuf + 2 * sz8)),
       "l"(T.tm_val), "r"(vx0), "r"(oy), "r"(mb)
       : "memory");
+}
+
+// The arrival a stalled staging withheld (test only).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
 
 // Waits for phase `parity` of the mbarrier; false when the wall-clock limit passed.
@@ -290,7 +306,7 @@ __device__ __forceinline__ bool tma_usable(const TileDev& T, const JobDev& J, co
          tma_stage_bytes(J) <= bytes;
 }
 
-// z(m, n) = (w, w*r) from the landed boxes; same thread mapping and the same
+// z(m, n) = (w, r) from the landed boxes; same thread mapping and the same
 // arithmetic as stage_support.
 template <int F>
 __device__ __forceinline__ void stage_from_boxes(const TileDev& T, const JobDev& J, int I, int Jb,
@@ -312,24 +328,74 @@ __device__ __forceinline__ void stage_from_boxes(const TileDev& T, const JobDev&
   const bool col_in = tx >= 0 && tx < T.ew;
   for (int m = m0; m < S; m += mstep) {
     const int ty = oy + m;
-    float wv = 0.f, zr = 0.f;
+    float wv = 0.f, rv = 0.f;
     if (col_in && ty >= 0 && ty < T.eh) {
       const float wi = __ldg(wiso + m * S + n);
       const int mk = smask[m * bw + dx8 + n];
       if (mk == 0) {
         wv = wi;
-        zr = wi * (float)simg[m * bw + dx8 + n];
+        rv = (float)simg[m * bw + dx8 + n];
       } else if (use_done) {
         const float v = sval[m * bv + dxv + n];
         if (!isnan(v)) {
           wv = delta * wi;
-          zr = wv * v;
+          rv = v;
         }
       }
     }
-    zbuf[swz<F>(m, n)] = make_float2(wv, zr);
+    zbuf[swz<F>(m, n)] = make_float2(wv, rv);
   }
 }
+
+// ---------------------------------------------------------------------------
+// Weighted mean c = sum(w r) / sum(w) of a staged support (z = (w, r)).
+// The FP32 executors transform w (r - c) instead of w r and then form
+// R_w = c W + DFT(w (r - c)), which is DFT(w r) exactly in real arithmetic:
+// the FFT's rounding error scales with the norm of its input, and the
+// support's mean dominates that norm, so taking it out before the transform
+// and adding it back through W (the spectrum the iteration subtracts from)
+// keeps R_w consistent with W to the precision of the small remainder.
+// Any c gives the same mathematics; the mean makes the remainder smallest.
+// Every thread of the group sums in the same fixed order, so all get the same
+// bits whichever staging path filled the buffer.  red: NT/32 floats (CTA).
+// ---------------------------------------------------------------------------
+template <int F, int NT>
+__device__ __forceinline__ float support_mean(const float2* zbuf, int S, int t, float* red) {
+  float sw = 0.f, swr = 0.f;
+  const int n = t & (F - 1);
+  if (n < S)
+    for (int m = t / F; m < S; m += NT / F) {
+      const float2 z = zbuf[swz<F>(m, n)];
+      sw += z.x;
+      swr = fmaf(z.x, z.y, swr);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    swr += __shfl_xor_sync(0xffffffffu, swr, o);
+  }
+  if constexpr (NT > 32) {
+    const int warp = t >> 5;
+    __syncthreads();
+    if ((t & 31) == 0) {
+      red[2 * warp] = sw;
+      red[2 * warp + 1] = swr;
+    }
+    __syncthreads();
+    sw = red[0];
+    swr = red[1];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) {
+      sw += red[2 * w];
+      swr += red[2 * w + 1];
+    }
+    __syncthreads();
+  }
+  return sw > 0.f ? swr / sw : 0.f;
+}
+
+// The row-FFT input w (r - c) from a staged pixel (w, r).
+__device__ __forceinline__ float2 centred(float2 z, float c) { return make_float2(z.x, (z.y - c) * z.x); }
 
 // ---------------------------------------------------------------------------
 // Register FFT (radix-2 decimation in time, natural order in and out):
@@ -687,9 +753,12 @@ constexpr size_t SMEM32 = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32);
 // Prologue of one F = 32 block: descriptors into shared memory, the support
 // staged into zbuf (32 x 32, swizzled), row FFTs in place, then the column
 // FFTs into registers: x[k1] = Z(k1, lane).
+// Returns false when the TMA staging's bounded wait ran out: the error is
+// flagged, the copies in flight are waited for (bounded again), and the warp
+// must stop (its buffer and mbarrier phase are no longer in a known state).
 template <class WS>
-__device__ __forceinline__ void stage_fft32(const ExecArgs& a, int id, WS& sm, float2* zbuf, int lane,
-                                            float2 (&x)[32], unsigned char* sbuf, int sbytes) {
+__device__ __forceinline__ bool stage_fft32(const ExecArgs& a, int id, WS& sm, float2* zbuf, int lane,
+                                            float2 (&x)[32], unsigned char* sbuf, int sbytes, float& rbar) {
   const ClassArgs& C = a.c[CLS_F32_32];
   const int2 it = C.items[id];
   copy_desc(&sm.T, a.tiles + it.x, lane, 32);
@@ -704,10 +773,17 @@ __device__ __forceinline__ void stage_fft32(const ExecArgs& a, int id, WS& sm, f
   if (lane == 0) debug_record(a, CLS_F32_32, id, T, it.x, I, Jb);
   if (tma_usable(T, J, sbuf, sbytes)) {
     const uint32_t ph = sm.tma_ph;
-    if (lane == 0) tma_issue_support(T, J, I, Jb, sbuf, &sm.mbar);
-    if (!mbar_wait(&sm.mbar, ph & 1, a.timeout_ns)) {
-      if (lane == 0) atomicOr(&C.q->error, ERR_TIMEOUT);
+    if (lane == 0) tma_issue_support(T, J, I, Jb, sbuf, &sm.mbar, a.dbg_tma_stall != 0);
+    // every lane waits with its own clock; the warp agrees on the outcome
+    if (!__all_sync(0xffffffffu, mbar_wait(&sm.mbar, ph & 1, a.timeout_ns))) {
+      if (lane == 0) {
+        atomicOr(&C.q->error, ERR_TIMEOUT);
+        if (a.dbg_tma_stall) mbar_arrive(&sm.mbar);
+      }
+      __syncwarp();
       mbar_wait(&sm.mbar, ph & 1, a.timeout_ns);  // the copies in flight, bounded again
+      __syncwarp();
+      return false;
     }
     stage_from_boxes<32>(T, J, I, Jb, zbuf, sbuf, lane, 32);
     __syncwarp();
@@ -716,10 +792,11 @@ __device__ __forceinline__ void stage_fft32(const ExecArgs& a, int id, WS& sm, f
     stage_support<32, float, float2>(T, J, val, I, Jb, zbuf, lane, 32);
   }
   __syncwarp();
-  // row FFTs: lane m transforms support row m
+  const float c = support_mean<32, 32>(zbuf, S, lane, nullptr);
+  // row FFTs of w (r - c): lane m transforms support row m
   if (lane < S) {
 #pragma unroll
-    for (int n = 0; n < 32; ++n) x[n] = n < S ? zbuf[swz<32>(lane, n)] : make_float2(0.f, 0.f);
+    for (int n = 0; n < 32; ++n) x[n] = n < S ? centred(zbuf[swz<32>(lane, n)], c) : make_float2(0.f, 0.f);
     fft_reg<32>(x);
 #pragma unroll
     for (int n = 0; n < 32; ++n) zbuf[swz<32>(lane, n)] = x[n];
@@ -730,21 +807,25 @@ __device__ __forceinline__ void stage_fft32(const ExecArgs& a, int id, WS& sm, f
   for (int m = 0; m < 32; ++m) x[m] = m < S ? zbuf[swz<32>(m, lane)] : make_float2(0.f, 0.f);
   fft_reg<32>(x);
   __syncwarp();
+  rbar = c;
+  return true;
 }
 
-__device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem32& sm, const float2* tw,
+__device__ __forceinline__ bool item_f32_32(const ExecArgs& a, int id, WarpSmem32& sm, const float2* tw,
                             int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
   float2 x[32];
   // stage -> rows 32..63 (swizzled F x F buffer); TMA boxes in rows 0..31
-  stage_fft32(a, id, sm, sm.Wd + 32 * 32, lane, x, reinterpret_cast<unsigned char*>(sm.Wd), 8192);
+  float rbar;
+  if (!stage_fft32(a, id, sm, sm.Wd + 32 * 32, lane, x, reinterpret_cast<unsigned char*>(sm.Wd), 8192, rbar)) return false;
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
   const int K = J.K;
   float* val = a.val_f + T.val_off;
-  // Hermitian split: W = (Z(k) + conj Z(-k))/2, R = (Z(k) - conj Z(-k))/(2i)
+  // Hermitian split: W = (Z(k) + conj Z(-k))/2, R' = (Z(k) - conj Z(-k))/(2i),
+  // R_w = rbar W + R'
   const int src = (32 - lane) & 31;
 #pragma unroll
   for (int j = 0; j <= 16; ++j) {
@@ -758,25 +839,25 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
     const float2 w = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
     sm.Wd[j * 32 + lane] = w;
     sm.Wd[(j + 32) * 32 + lane] = w;
-    x[j] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    x[j] = make_float2(fmaf(rbar, w.x, 0.5f * (z.y + zm.y)), fmaf(rbar, w.y, 0.5f * (zm.x - z.x)));
     if (j2 != j) {
       const float2 w2 = make_float2(0.5f * (z2.x + zm2.x), 0.5f * (z2.y - zm2.y));
       sm.Wd[j2 * 32 + lane] = w2;
       sm.Wd[(j2 + 32) * 32 + lane] = w2;
-      x[j2] = make_float2(0.5f * (z2.y + zm2.y), 0.5f * (zm2.x - z2.x));
+      x[j2] = make_float2(fmaf(rbar, w2.x, 0.5f * (z2.y + zm2.y)), fmaf(rbar, w2.y, 0.5f * (zm2.x - z2.x)));
     }
   }
   __syncwarp();
   const float W0 = sm.Wd[0].x;
   if (!(W0 > 0.f)) {  // no usable pixel in the support
     if (lane == 0) atomicAdd(&C.q->n_empty, 1);
-    return;
+    return true;
   }
   const float gs = J.gamma_f / W0;
   float2(&R)[32] = x;
 
-  // key: energy bits with the low 5 bits replaced by 31 - row; ties between
-  // lanes (equal keys) go to the lowest lane, i.e. the lowest flat index
+  // key: energy bits with the low 5 bits replaced by 31 - row; equal keys go
+  // to the lowest lane, i.e. the lowest flat index
   const uint32_t kmask = opaque(0xFFFFFFE0u);
   uint32_t bq[2] = {0u, 0u};  // two independent max chains, three-input max
   static_for<0, 16>([&](auto h) {
@@ -825,6 +906,7 @@ __device__ __forceinline__ void item_f32_32(const ExecArgs& a, int id, WarpSmem3
     for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
   eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
                                        32);
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -848,13 +930,14 @@ struct alignas(128) WarpSmem32P {
   JobDev J;
 };
 
-__device__ __forceinline__ void item_f32_32p(const ExecArgs& a, int id, WarpSmem32P& sm, const float2* tw,
+__device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem32P& sm, const float2* tw,
                                              int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
   float2* zbuf = reinterpret_cast<float2*>(sm.Wt);
   float4* Wt = sm.Wt;
   float2 x[32];
-  stage_fft32(a, id, sm, zbuf, lane, x, reinterpret_cast<unsigned char*>(sm.Wt) + 8192, 35 * 32 * 16 - 8192);
+  float rbar;
+  if (!stage_fft32(a, id, sm, zbuf, lane, x, reinterpret_cast<unsigned char*>(sm.Wt) + 8192, 35 * 32 * 16 - 8192, rbar)) return false;
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -878,7 +961,7 @@ __device__ __forceinline__ void item_f32_32p(const ExecArgs& a, int id, WarpSmem
       const int col = p + 16 * c, colm = (32 - col) & 31;
       const float2 z = zbuf[swz<32>(k1, col)], zm = zbuf[swz<32>(k1m, colm)];
       w[c] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-      r[c] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+      r[c] = make_float2(fmaf(rbar, w[c].x, 0.5f * (z.y + zm.y)), fmaf(rbar, w[c].y, 0.5f * (zm.x - z.x)));
     }
     RX[pi] = make_float2(r[0].x, r[1].x);
     RY[pi] = make_float2(r[0].y, r[1].y);
@@ -905,7 +988,7 @@ __device__ __forceinline__ void item_f32_32p(const ExecArgs& a, int id, WarpSmem
   const float W0 = Wt[0].x;
   if (!(W0 > 0.f)) {  // no usable pixel in the support
     if (lane == 0) atomicAdd(&C.q->n_empty, 1);
-    return;
+    return true;
   }
   const float gs = J.gamma_f / W0;
   // key: energy bits with the low 5 bits replaced by 31 - l, l = 2 pi + c
@@ -966,6 +1049,7 @@ __device__ __forceinline__ void item_f32_32p(const ExecArgs& a, int id, WarpSmem
     for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
   eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
                                        32);
+  return true;
 }
 constexpr size_t SMEM32P = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32P);
 
@@ -988,18 +1072,20 @@ struct alignas(128) WarpSmem32R {
   JobDev J;
 };
 
-__device__ __forceinline__ void item_f32_32r(const ExecArgs& a, int id, WarpSmem32R& sm, const float2* tw,
+__device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WarpSmem32R& sm, const float2* tw,
                                              int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
   float2 x[32];
-  stage_fft32(a, id, sm, sm.Wd, lane, x, reinterpret_cast<unsigned char*>(sm.Wd) + 8192, 7680);
+  float rbar;
+  if (!stage_fft32(a, id, sm, sm.Wd, lane, x, reinterpret_cast<unsigned char*>(sm.Wd) + 8192, 7680, rbar)) return false;
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
   const int K = J.K;
   float* val = a.val_f + T.val_off;
-  // Hermitian split from registers (the FFT buffer is no longer read)
+  // Hermitian split from registers (the FFT buffer is no longer read),
+  // R_w = rbar W + R'
   const int src = (32 - lane) & 31;
 #pragma unroll
   for (int j = 0; j <= 16; ++j) {
@@ -1013,23 +1099,23 @@ __device__ __forceinline__ void item_f32_32r(const ExecArgs& a, int id, WarpSmem
     const float2 w = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
     sm.Wd[j * 32 + lane] = w;
     if (j < 3) sm.Wd[(j + 32) * 32 + lane] = w;
-    x[j] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+    x[j] = make_float2(fmaf(rbar, w.x, 0.5f * (z.y + zm.y)), fmaf(rbar, w.y, 0.5f * (zm.x - z.x)));
     if (j2 != j) {
       const float2 w2 = make_float2(0.5f * (z2.x + zm2.x), 0.5f * (z2.y - zm2.y));
       sm.Wd[j2 * 32 + lane] = w2;
-      x[j2] = make_float2(0.5f * (z2.y + zm2.y), 0.5f * (zm2.x - z2.x));
+      x[j2] = make_float2(fmaf(rbar, w2.x, 0.5f * (z2.y + zm2.y)), fmaf(rbar, w2.y, 0.5f * (zm2.x - z2.x)));
     }
   }
   __syncwarp();
   const float W0 = sm.Wd[0].x;
   if (!(W0 > 0.f)) {  // no usable pixel in the support
     if (lane == 0) atomicAdd(&C.q->n_empty, 1);
-    return;
+    return true;
   }
   const float gs = J.gamma_f / W0;
   float2(&R)[32] = x;
-  // key: energy bits with the low 5 bits replaced by 31 - row; equal keys go
-  // to the lowest lane, i.e. the lowest flat index
+  // key: energy bits with the low 5 bits replaced by 31 - row; ties between
+  // lanes (equal keys) go to the lowest lane, i.e. the lowest flat index
   const uint32_t kmask = opaque(0xFFFFFFE0u);
   uint32_t bq[2] = {0u, 0u};
   static_for<0, 16>([&](auto h) {
@@ -1081,14 +1167,15 @@ __device__ __forceinline__ void item_f32_32r(const ExecArgs& a, int id, WarpSmem
     for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
   eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
                                        32);
+  return true;
 }
 constexpr size_t SMEM32R = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32R);
 
 template <class WS>
-__device__ __forceinline__ void run_item32(const ExecArgs& a, int id, WS& sm, const float2* tw, int lane) {
-  if constexpr (std::is_same<WS, WarpSmem32P>::value) item_f32_32p(a, id, sm, tw, lane);
-  else if constexpr (std::is_same<WS, WarpSmem32R>::value) item_f32_32r(a, id, sm, tw, lane);
-  else item_f32_32(a, id, sm, tw, lane);
+__device__ __forceinline__ bool run_item32(const ExecArgs& a, int id, WS& sm, const float2* tw, int lane) {
+  if constexpr (std::is_same<WS, WarpSmem32P>::value) return item_f32_32p(a, id, sm, tw, lane);
+  else if constexpr (std::is_same<WS, WarpSmem32R>::value) return item_f32_32r(a, id, sm, tw, lane);
+  else return item_f32_32(a, id, sm, tw, lane);
 }
 
 template <class WS>
@@ -1114,13 +1201,16 @@ __global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32R>::valu
   if (a.level_mode) {
     const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x * NW32 + warp; id < n; id += gridDim.x * NW32)
-      if (a.level_of[(size_t)CLS_F32_32 * a.level_stride + id] == a.level) run_item32(a, id, sm, tw, lane);
+      if (a.level_of[(size_t)CLS_F32_32 * a.level_stride + id] == a.level)
+        if (!run_item32(a, id, sm, tw, lane)) break;
     return;
   }
   for (;;) {
     const int id = queue_pop_warp(C, a.timeout_ns, lane);
     if (id < 0) break;
-    run_item32(a, id, sm, tw, lane);
+    if (!run_item32(a, id, sm, tw, lane)) break;  // staging timed out: this warp stops
+    // value-plane stores before later blocks' TMA (asynchronous-proxy) reads
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     __threadfence();
     __syncwarp();
     const int2 it = C.items[id];
@@ -1155,7 +1245,7 @@ struct alignas(16) CtaSmem64 {
 // staged into zbuf (64 x 64, swizzled) and transformed in place by the 2-D FFT.
 // Ends behind a barrier.
 template <int NT, class Sm>
-__device__ __forceinline__ void stage_fft64(const ExecArgs& a, int id, Sm& sm, float2* zbuf, int t) {
+__device__ __forceinline__ float stage_fft64(const ExecArgs& a, int id, Sm& sm, float2* zbuf, int t) {
   const ClassArgs& C = a.c[CLS_F32_64];
   const int2 it = C.items[id];
   copy_desc(&sm.T, a.tiles + it.x, t, NT);
@@ -1171,7 +1261,8 @@ __device__ __forceinline__ void stage_fft64(const ExecArgs& a, int id, Sm& sm, f
 
   stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, NT);
   __syncthreads();
-  // 64-point lines on lane pairs (l, l ^ 16): half h transforms the samples
+  const float c = support_mean<64, NT>(zbuf, S, t, sm.red);
+  // rows of w (r - c), 64-point lines on lane pairs (l, l ^ 16): half h transforms the samples
   // 2n + h (32 points), then X[k + 32h] = E[k] +- exp(-2 pi i k/64) O[k].
   // NT/2 lines per pass.
   for (int lb = 0; lb < 64; lb += NT / 2) {
@@ -1184,7 +1275,8 @@ __device__ __forceinline__ void stage_fft64(const ExecArgs& a, int id, Sm& sm, f
       const bool live = line < S;
 #pragma unroll
       for (int n = 0; n < 32; ++n)
-        x[n] = live && 2 * n + h < S ? zbuf[swz<64>(live ? line : 0, 2 * n + h)] : make_float2(0.f, 0.f);
+        x[n] = live && 2 * n + h < S ? centred(zbuf[swz<64>(live ? line : 0, 2 * n + h)], c)
+                                     : make_float2(0.f, 0.f);
       fft_reg<32>(x);
       fft64_combine(x, h);
       if (live) {
@@ -1209,6 +1301,7 @@ __device__ __forceinline__ void stage_fft64(const ExecArgs& a, int id, Sm& sm, f
     }
   }
   __syncthreads();
+  return c;
 }
 
 template <int NWB, int ROWS>
@@ -1216,7 +1309,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   constexpr int NT = NWB * 32, RPT = 4096 / NT;
   const ClassArgs& C = a.c[CLS_F32_64];
   float2* zbuf = ROWS == 128 ? sm.Wd + 64 * 64 : sm.Wd;
-  stage_fft64<NT>(a, id, sm, zbuf, t);
+  const float rbar = stage_fft64<NT>(a, id, sm, zbuf, t);
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -1231,8 +1324,9 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     for (int i = 0; i < RPT; ++i) {
       const int k1 = i + RPT * q, k1m = (64 - k1) & 63;
       const float2 z = zbuf[swz<64>(k1, c)], zm = zbuf[swz<64>(k1m, cm)];
-      sm.Wd[k1 * 64 + c] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-      R[i] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+      const float2 w = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      sm.Wd[k1 * 64 + c] = w;
+      R[i] = make_float2(fmaf(rbar, w.x, 0.5f * (z.y + zm.y)), fmaf(rbar, w.y, 0.5f * (zm.x - z.x)));
     }
     __syncthreads();
 #pragma unroll
@@ -1242,13 +1336,14 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     }
     __syncthreads();
   } else {
-    // R = (Z(k) - conj Z(-k)) / 2i into registers (reads only)
+    // R = rbar W + (Z(k) - conj Z(-k)) / 2i into registers (reads only)
     const int cm = (64 - c) & 63;
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
       const int k1 = i + RPT * q, k1m = (64 - k1) & 63;
       const float2 z = zbuf[swz<64>(k1, c)], zm = zbuf[swz<64>(k1m, cm)];
-      R[i] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+      R[i] = make_float2(fmaf(rbar, 0.5f * (z.x + zm.x), 0.5f * (z.y + zm.y)),
+                         fmaf(rbar, 0.5f * (z.y - zm.y), 0.5f * (zm.x - z.x)));
     }
     __syncthreads();
     // W = (Z(k) + conj Z(-k)) / 2 in place, unswizzled.  The swizzle permutes
@@ -1375,7 +1470,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
   const ClassArgs& C = a.c[CLS_F32_64];
   float2* zbuf = sm.Wd;  // the FFT buffer is table rows 0..31
   float4* Wt = reinterpret_cast<float4*>(sm.Wd);
-  stage_fft64<NT>(a, id, sm, zbuf, t);
+  const float rbar = stage_fft64<NT>(a, id, sm, zbuf, t);
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -1384,8 +1479,8 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
   float* val = a.val_f + T.val_off;
   const int p = t & 31, g = t >> 5, lane = p, warp = g;
 
-  // Hermitian split of Z = DFT(w + i w r): W = (Z(k) + conj Z(-k)) / 2 into
-  // the table, R = (Z(k) - conj Z(-k)) / 2i into registers.  Table rows >= 32
+  // Hermitian split of Z = DFT(w + i w (r - rbar)): W = (Z(k) + conj Z(-k)) / 2
+  // into the table, R = rbar W + (Z(k) - conj Z(-k)) / 2i into registers.  Table rows >= 32
   // lie past the FFT buffer and are written at once; rows < 32 wait for every
   // thread's reads.
   float2 RX[16], RY[16];
@@ -1399,7 +1494,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
       const int col = p + 32 * h, colm = (64 - col) & 63;
       const float2 z = zbuf[swz<64>(k1, col)], zm = zbuf[swz<64>(k1m, colm)];
       w[h] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-      r[h] = make_float2(0.5f * (z.y + zm.y), 0.5f * (zm.x - z.x));
+      r[h] = make_float2(fmaf(rbar, w[h].x, 0.5f * (z.y + zm.y)), fmaf(rbar, w[h].y, 0.5f * (zm.x - z.x)));
     }
     RX[pi] = make_float2(r[0].x, r[1].x);
     RY[pi] = make_float2(r[0].y, r[1].y);

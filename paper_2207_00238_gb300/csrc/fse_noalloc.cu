@@ -38,7 +38,6 @@ struct DeviceSetup {
   bool done = false;
   unsigned char* scratch = nullptr;  // device address of g_scratch on this device
   int sm_count = 0;
-  int occupancy[MAX_CLS] = {1, 1, 1};
 };
 DeviceSetup g_setup[kMaxDevices];
 
@@ -70,13 +69,6 @@ int setup(int dev) {
   set_twiddles(twf, twd);
   e = exec_setup(dev);
   if (e != cudaSuccess) return cuda_fail(e, "kernel set-up");
-  for (int k = 0; k < MAX_CLS; ++k) {
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(k), exec_threads(k),
-                                                      exec_smem(k));
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
-    s.occupancy[k] = nb > 0 ? nb : 1;
-  }
   s.done = true;
   return FSE_OK;
 }
@@ -241,9 +233,17 @@ int run(const fse_job_t* jobs, int32_t n, cudaStream_t st) {
   for (int k = 0; k < MAX_CLS; ++k)
     if (cap[k] > 0) NOALLOC_CUDA(launch_deps(a, k, (int)cap[k], st));
   for (int k = 0; k < MAX_CLS; ++k)
-    if (cap[k] > 0) NOALLOC_CUDA(launch_exec(a, k, S.occupancy[k] * S.sm_count, st));
+    if (cap[k] > 0) {
+      // the executor layout of a class can change between calls (options,
+      // autotuner), so the persistent grid is sized for the current one
+      int nb = 0;
+      NOALLOC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(k), exec_threads(k),
+                                                                 exec_smem(k)));
+      NOALLOC_CUDA(launch_exec(a, k, (nb > 0 ? nb : 1) * S.sm_count, st));
+    }
+  // the queue state comes back on the caller's stream: no device-wide sync
+  NOALLOC_CUDA(cudaMemcpyAsync(g_q, base + o_q, sizeof(g_q), cudaMemcpyDeviceToHost, st));
   NOALLOC_CUDA(cudaStreamSynchronize(st));
-  NOALLOC_CUDA(cudaMemcpy(g_q, base + o_q, sizeof(g_q), cudaMemcpyDeviceToHost));
 #undef NOALLOC_CUDA
   int err = 0;
   for (int k = 0; k < MAX_CLS; ++k) err |= g_q[k].error;
