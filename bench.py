@@ -1,11 +1,15 @@
 #!/usr/bin/env python
 """Benchmark: FSE lost-blocks/s (and Mpix/s, % roofline) on one GB300.
 
-Default workload: one 1024x1024 8-bit image with 20 % of its 8x8 blocks lost
-(bursts + isolated), b=8, B=16, F=64, K=200, tiled by Algorithm 1 into 16
-overlapping tiles (d=32), all tiles in one call.  A step is one full pass of
-the method (tiling, lost-block enumeration and ordering, staging, DFT,
-K iterations, model evaluation, write-back) over that input.
+Default workload: the 256-image batch -- images of uneven seeded sizes from
+256x256 to 2048x1536, 5-50 % of their 4x4 (F=32, K=100) or 8x8 (F=64, K=200)
+blocks lost, supports truncated at the image borders, ~2.8 M lost blocks,
+both DFT classes in one call (the largest single-GPU workload).  A step is one
+full pass of the method (tiling, lost-block enumeration and ordering, staging,
+DFT, K iterations, model evaluation, write-back) over that input.
+--workload tiled_1024 (one 1024^2 image, 16 tiles of Algorithm 1, F=64,
+K=200), defects_4k (3840x2160 defect-pixel image, F=32) and plain_64 select
+the other workloads.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -52,14 +56,16 @@ def captured_traffic(workload):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: ~6 s of steps)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tiled_1024")
+    ap.add_argument("--workload", default="batch_256")
     ap.add_argument("--mode", default="dag", choices=["dag", "levels", "per_block"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="oracle seconds per CPU-baseline leg (all cores, then one core)")
+    ap.add_argument("--no-per-block", action="store_true", help="skip the per-block launch baseline")
     ap.add_argument("--arena-mb", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="measured requests of the serving leg (0 = skip)")
@@ -167,14 +173,16 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_blocks_per_s(job, seconds, max_blocks=None):
+def oracle_blocks_per_s(job, seconds, max_blocks=None, threads=0):
+    """The oracle on the first blocks of one job (processing order, tile 0
+    first) for about `seconds`: (blocks/s, blocks, seconds, threads used)."""
     import oracle
     oracle.build()
     p = job["params"]
     kw = dict(block=p["block"], border=p["border"], fft=p["fft"], K=p["K"], rho=p["rho"],
               delta=p["delta"], gamma=p["gamma"], order=p["order"], n_tiles=p["n_tiles"],
-              overlap=p["overlap"])
-    cores = oracle.threads()
+              overlap=p["overlap"], threads=threads)
+    cores = threads if threads > 0 else oracle.threads()
     if max_blocks is None:
         probe = max(cores, 4)
         t = time.perf_counter()
@@ -189,26 +197,61 @@ def oracle_blocks_per_s(job, seconds, max_blocks=None):
     return n / dt, n, dt, cores
 
 
+def oracle_mix_rate(jobs, class_blocks, seconds, threads=0):
+    """Oracle throughput on the workload's mix of DFT classes: each class
+    present is timed on the first blocks of its first job (about
+    seconds / classes each) and the per-class rates r_k are combined with the
+    workload's block shares f_k as 1 / sum_k f_k / r_k.  Returns
+    (blocks/s, description, threads)."""
+    shares = {32: class_blocks[0], 64: class_blocks[1]}
+    total = sum(shares.values())
+    present = [F for F in (32, 64) if shares[F] > 0]
+    inv, parts, cores = 0.0, [], 0
+    for F in present:
+        job = next(j for j in jobs if j["params"]["fft"] == F)
+        rate, n, dt, cores = oracle_blocks_per_s(job, seconds / len(present), threads=threads)
+        inv += (shares[F] / total) / rate
+        parts.append(f"F={F}: first {n} blocks of its first image, {dt:.1f} s, {rate:.1f} blocks/s, "
+                     f"{100 * shares[F] / total:.1f} % of the workload's blocks")
+    return 1.0 / inv, "; ".join(parts), cores
+
+
+def class_blocks_of(jobs):
+    """Lost blocks per DFT class (F=32, F=64) counted from the masks and tilings."""
+    import oracle
+    out = [0, 0]
+    for j in jobs:
+        p = j["params"]
+        b = p["block"]
+        rc, tiles = oracle.plan_tiles(j["image"].shape[1], j["image"].shape[0], p["n_tiles"], p["overlap"])
+        for (x, y, w, h, ex, ey, ew, eh) in tiles:
+            m = j["mask"][ey:ey + eh, ex:ex + ew]
+            nby, nbx = -(-eh // b), -(-ew // b)
+            pad = np.zeros((nby * b, nbx * b), np.uint8)
+            pad[:eh, :ew] = m
+            out[0 if p["fft"] == 32 else 1] += int((pad.reshape(nby, b, nbx, b).max(axis=(1, 3)) > 0).sum())
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     jobs = workload(args.workload)
-    job = jobs[0]
-    # ~150 s of oracle work for the whole run, whatever K and W (at least 16 blocks a step)
-    per_step = max(0.05, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
-    _, n, _, cores = oracle_blocks_per_s(job, per_step)
+    steps = args.steps if args.steps is not None else 5
+    cb = class_blocks_of(jobs)
+    # ~150 s of oracle work for the whole run, whatever K and W
+    per_step = max(0.1, min(30.0, 150.0 / max(steps + args.warmup, 1)))
     for _ in range(args.warmup):
-        oracle_blocks_per_s(job, per_step, max_blocks=n)
-    tot_n, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        _, nn, dt, _ = oracle_blocks_per_s(job, per_step, max_blocks=n)
-        tot_n += nn
-        tot_t += dt
-    value = tot_n / tot_t
-    sample = (f"first {n} lost blocks (processing order, tile 0 first) of the {args.workload} "
-              f"workload per step, FP64 spatial-domain oracle, {cores} threads")
+        oracle_mix_rate(jobs, cb, per_step)
+    rates, desc, cores = [], "", 0
+    for _ in range(steps):
+        r, desc, cores = oracle_mix_rate(jobs, cb, per_step)
+        rates.append(r)
+    value = len(rates) / sum(1.0 / r for r in rates)
+    tot_t = steps * per_step
+    sample = (f"per step: {desc}; FP64 spatial-domain oracle, {cores} threads")
     line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": describe(args.workload, jobs), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "blocks/s", "cores": cores, "kind": "oracle",
@@ -374,6 +417,48 @@ def run_study(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def describe_tuning(trace):
+    """The autotuner's trace: the fastest candidate per class (the one it
+    applied) and, for a mix, the class launch it chose."""
+    best = {}
+    for c, code, k, ms in trace:
+        c = int(c)
+        if c not in best or ms < best[c][3]:
+            best[c] = (c, int(code), int(k), ms)
+    out = {"candidates": len(trace), "chosen": {}}
+    for c, (_, code, k, ms) in sorted(best.items()):
+        if c < 0:
+            out["class_launch"] = {0: "sequential", 1: "concurrent, F=64 first",
+                                   2: "concurrent, F=32 first"}[code]
+        else:
+            out["chosen"][c] = {"layout": code // 10, "unroll": code % 10, "ctas_per_sm": k, "ms": round(ms, 4)}
+    return out
+
+
+def per_block_baseline(fse, ctx, cjobs, sptr, max_blocks=6000):
+    """Blocks/s of the plain per-block launch (FSE_EXEC_PER_BLOCK: one kernel
+    launch per lost block, in processing order) on the first jobs of the
+    workload holding up to max_blocks blocks, and of the batched persistent
+    launch on the same jobs."""
+    sub, nb = [], 0
+    for j in cjobs:
+        sub.append(j)
+        st = ctx.extrapolate(sub, stream=sptr, stats=True)
+        nb = st["lost_blocks"]
+        if nb >= max_blocks:
+            break
+    st_dag = ctx.extrapolate(sub, stream=sptr, stats=True)
+    ctx.exec_mode("per_block")
+    try:
+        st_pb = ctx.extrapolate(sub, stream=sptr, stats=True)
+    finally:
+        ctx.exec_mode("dag")
+    return {"value": st_pb["lost_blocks"] / (st_pb["device_ms"] / 1000.0), "unit": "blocks/s",
+            "launches": st_pb["launches"],
+            "batched_same_sample": st_dag["lost_blocks"] / (st_dag["device_ms"] / 1000.0),
+            "sample": f"the first {len(sub)} images of the workload, {st_pb['lost_blocks']} lost blocks"}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -421,22 +506,24 @@ def main():
     tuned = None
     if not args.no_autotune and not args.f64_warps and not args.f32_layout and not args.ctas_per_sm and args.mode == "dag":
         trace = ctx.autotune(cjobs, stream=sptr, reps=3)
-        tuned = {"candidates": len(trace),
-                 "chosen": {int(c): {"layout": int(l), "ctas_per_sm": int(k), "ms": round(ms, 4)}
-                            for c, l, k, ms in sorted(trace, key=lambda r: r[3])[::-1]}}
-    # one counted pass: blocks per step, bin-iterations per step
+        tuned = describe_tuning(trace)
+    # one counted pass: blocks per step, bin-iterations per step (per class)
     st = ctx.extrapolate(cjobs, stream=sptr, stats=True)
     blocks, core_blocks, bins = st["lost_blocks"], st["core_lost_blocks"], st["bin_iterations"]
+    cls_blocks, cls_bins = st["class_blocks"], st["class_bin_iterations"]
     launches_per_step = st["launches"]
+    step_est = st["device_ms"] / 1000.0
+    steps = args.steps if args.steps is not None else int(min(400, max(10, 6.0 / max(step_est, 1e-4))))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     # the iteration kernels' durations: a pass of their own without graph
     # replay (kernel-timing events are not captured into the graph)
     ctx.set_option(fse.OPT_KERNEL_TIMING, 1)
     ctx.kernel_times()
-    for i in range(max(3, min(args.steps, 50))):
+    for i in range(max(3, min(steps, 50))):
         flush.fill_(float(i))
         ctx.extrapolate(cjobs, stream=sptr, stats=False)
     torch.cuda.synchronize()
+    cls_ms = ctx.class_times()
     kern_ms = ctx.kernel_times()
     ctx.set_option(fse.OPT_KERNEL_TIMING, 0)
     # the timed steps replay the call's CUDA graph (captured on the first call)
@@ -444,8 +531,8 @@ def main():
         ctx.set_option(fse.OPT_USE_GRAPH, 1)
     for _ in range(args.warmup):
         ctx.extrapolate(cjobs, stream=sptr, stats=False)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -453,7 +540,7 @@ def main():
                     if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
     clocks.start()
     time.sleep(0.3)
-    for i in range(args.steps):
+    for i in range(steps):
         flush.fill_(float(i))  # evict the inputs from L2 between steps
         starts[i].record(stream)
         ctx.extrapolate(cjobs, stream=sptr, stats=False)
@@ -465,11 +552,12 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ctx.set_option(fse.OPT_USE_GRAPH, 0)
     total_s = max_over_ranks(sum(step_ms) / 1000.0, dist, dev)
-    value = whole_job_rate(blocks, world, args.steps, total_s)
-    mpix = world * pix * args.steps / total_s / 1e6
+    value = whole_job_rate(blocks, world, steps, total_s)
+    mpix = world * pix * steps / total_s / 1e6
 
-    # roofline of the dominant kernel (the iteration loop): algorithmic shared-
-    # memory bytes (8 B of W per bin-iteration) / its event-timed duration
+    # roofline of the iteration kernels: algorithmic shared-memory bytes (8 B of
+    # W per bin-iteration) / event-timed duration, for the call's whole
+    # execution (the classes run concurrently) and per class
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peaks = {}
@@ -482,14 +570,27 @@ def main():
     peak_gbs = SMEM_BYTES_PER_CLK_SM * sms * f_max * 1e6 / 1e9
     kmean = statistics.mean(kern_ms) if kern_ms else float("nan")
     achieved = bins * BYTES_PER_BIN_ITER / (kmean / 1000.0) / 1e9
+    names = {0: "k_exec_f32_32", 1: "k_exec_f32_64"}
+    per_class = {}
+    for k in (0, 1):
+        if cls_blocks[k] <= 0:
+            continue
+        ms_k = statistics.mean(r[k] for r in cls_ms) if cls_ms else float("nan")
+        ach_k = cls_bins[k] * BYTES_PER_BIN_ITER / (ms_k / 1000.0) / 1e9 if cls_bins[k] > 0 else None
+        per_class[names[k]] = {"blocks_per_launch": cls_blocks[k], "bin_iterations_per_launch": cls_bins[k],
+                               "kernel_ms": ms_k, "achieved": ach_k,
+                               "frac": ach_k / peak_gbs if ach_k else None}
     roof = {"bound": "alu", "pipe": "shared-memory (LSU) pipe, 128 B/clk/SM",
             "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
             "traffic": captured_traffic(args.workload),
             "traffic_note": "DRAM bytes per launch (ncu); the kernel's bound is on chip",
-            "kernel": "+".join(sorted({"k_exec_f32_64" if j["params"]["fft"] == 64 else "k_exec_f32_32"
-                                       for j in jobs})),
+            "kernel": "+".join(names[k] for k in (0, 1) if cls_blocks[k] > 0),
             "kernel_ms": kmean, "bin_iterations_per_launch": bins,
-            "peak_basis": f"derived: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {sms} SMs x {f_max:.0f} MHz"}
+            "peak_basis": f"derived: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {sms} SMs x {f_max:.0f} MHz",
+            "per_class": per_class}
+    if len(per_class) > 1:
+        roof["per_class_note"] = ("with FSE_OPT_CLASS_LAUNCH concurrent the classes share the GPU, so a "
+                                  "class's fraction counts its own launch span against the whole GPU")
     if clk:
         roof["frac_at_observed_clock"] = achieved / (SMEM_BYTES_PER_CLK_SM * sms * clk["sm_mhz"] * 1e6 / 1e9)
     # HBM side of the step: support staging and write-back are fused into the
@@ -502,6 +603,13 @@ def main():
            "frac": hbm_gbs / hbm_peak, "dram_bytes_per_launch": captured_traffic(args.workload),
            "peak_basis": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback",
            "note": "staging and write-back are latency-bound parts of the on-chip-bound iteration kernel"}
+
+    # the plain per-block launch (one launch per lost block, in processing
+    # order) on a bounded sample of the workload, against the same sample in
+    # the batched persistent launch
+    per_block = None
+    if not args.no_per_block and args.mode == "dag":
+        per_block = per_block_baseline(fse, ctx, cjobs, sptr)
 
     # end to end through the host-buffer entry point (copies timed)
     e2e = None
@@ -520,13 +628,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(args.steps):
+        for i in range(steps):
             e2e_ctx.extrapolate_host(hj, stream=sptr)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
-        e2e = {"value": world * blocks * args.steps / e2e_s, "unit": "blocks/s",
+        e2e = {"value": world * blocks * steps / e2e_s, "unit": "blocks/s",
                "h2d_bytes_per_step": 2 * pix, "d2h_bytes_per_step": pix,
-               "mpix_per_s": world * pix * args.steps / e2e_s / 1e6}
+               "mpix_per_s": world * pix * steps / e2e_s / 1e6}
         e2e_ctx.close()
 
     serving = None
@@ -535,10 +643,12 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, n, dt, cores = oracle_blocks_per_s(jobs[0], args.cpu_seconds)
+        cb = [cls_blocks[0], cls_blocks[1]]
+        v, desc, cores = oracle_mix_rate(jobs, cb, args.cpu_seconds)
+        v1, desc1, _ = oracle_mix_rate(jobs, cb, args.cpu_seconds, threads=1)
         cpu = {"value": v, "unit": "blocks/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {n} lost blocks (processing order, tile 0 first) of the "
-                         f"{args.workload} workload, {dt:.1f} s, FP64 spatial-domain projections"}
+               "sample": f"{desc} (FP64 spatial-domain projections, {cores} threads)",
+               "one_core": {"value": v1, "unit": "blocks/s", "cores": 1, "sample": desc1}}
     if rank == 0:
         cfg = describe(args.workload, jobs)
         cfg.update({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -546,12 +656,12 @@ def main():
                     "lost_blocks_per_step": blocks, "core_lost_blocks_per_step": core_blocks,
                     "bin_iterations_per_step": bins})
         line = {"metric": "FSE lost-blocks/s", "value": value, "unit": "blocks/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1000 * total_s / args.steps, "higher_is_better": True,
+                "steps": steps, "warmup": args.warmup,
+                "ms_per_step": 1000 * total_s / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "mpix_per_s": mpix, "roofline": roof, "hbm": hbm, "cpu_baseline": cpu,
-                "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
-                "serving": serving}
+                "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * steps,
+                "plain_per_block": per_block, "serving": serving}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -131,6 +131,10 @@ typedef struct fse_stats_t {
     int32_t jobs, tiles, launches, graph_replayed;
     float device_ms;          /* stream time of the whole call (events)       */
     float exec_ms;            /* stream time of the iteration kernels         */
+    /* per work class (0: FP32 F = 32, 1: FP32 F = 64, 2: FP64): block runs,
+       and K*F*F over its modelled blocks (-1 when K varies within the class) */
+    int64_t class_blocks[3];
+    int64_t class_bin_iterations[3];
 } fse_stats_t;
 
 /* ---- context: one GPU, one device arena ---------------------------------- */
@@ -153,13 +157,13 @@ void fse_context_destroy(fse_context_t* ctx);
 #define FSE_OPT_USE_GRAPH 4     /* 1 = capture each batch in a CUDA graph and
                                    replay it while the job set is unchanged    */
 #define FSE_OPT_DEBUG_CAPTURE 5 /* 1 = record each block's selected bins       */
-#define FSE_OPT_F64_WARPS 7     /* layout of the F = 64 FP32 executor: warps per
+#define FSE_OPT_F64_WARPS 7     /* layout of this context's F = 64 FP32 executor: warps per
                                    block 2 (64 bins per thread), 4 (32) or 8 (16);
                                    5 = 4 warps with a 96-row W table (4 blocks
                                    per SM); 6 = 4 warps, bins paired for the
                                    two-wide FP32 instructions (W table of
                                    16-byte slots, 67 KB); 0 = default (6)      */
-#define FSE_OPT_F32_LAYOUT 8    /* layout of the F = 32 FP32 executor: 1 = one
+#define FSE_OPT_F32_LAYOUT 8    /* layout of this context's F = 32 executor: 1 = one
                                    spectrum column per lane, 2 = bins paired
                                    for the two-wide FP32 instructions, 3 = one
                                    column per lane read in row runs (35-row W
@@ -179,8 +183,19 @@ void fse_context_destroy(fse_context_t* ctx);
                                    (exercises the failure path, no fault)     */
 #define FSE_OPT_KERNEL_TIMING 6 /* 1 = bracket the iteration kernels of every
                                    call with CUDA events (no synchronisation);
-                                   read with fse_context_kernel_times         */
-#define FSE_EXEC_DAG 0       /* one persistent launch per DFT class; blocks start
+                                   read with fse_context_class_times and
+                                   fse_context_kernel_times                   */
+#define FSE_OPT_F32_UNROLL 11   /* K-loop unroll factor of the F = 32 executor:
+                                   1 (default) or 2 (layouts 2 and 3)          */
+#define FSE_OPT_F64_UNROLL 12   /* K-loop unroll factor of the F = 64 executor:
+                                   1 (default) or 2 (layout 6)                 */
+#define FSE_OPT_CLASS_LAUNCH 13 /* work classes of one call (F = 32, F = 64,
+                                   FP64): 0 = launched one after the other;
+                                   1 (default) = concurrently on forked streams,
+                                   the F = 64 class first; 2 = concurrently,
+                                   the F = 32 class first                      */
+#define FSE_EXEC_DAG 0       /* one persistent launch per work class, the classes
+                                concurrent (FSE_OPT_CLASS_LAUNCH); blocks start
                                 as soon as the blocks they depend on are done  */
 #define FSE_EXEC_LEVELS 1    /* one launch per order level (phase)            */
 #define FSE_EXEC_PER_BLOCK 2 /* one launch per lost block, in processing order */
@@ -189,22 +204,34 @@ int fse_context_set_option(fse_context_t* ctx, int32_t key, int64_t value);
 /*
  * fse_context_kernel_times -- with FSE_OPT_KERNEL_TIMING = 1: synchronises the
  * context's GPU, writes the elapsed milliseconds of the iteration kernels of
- * each call since the option was set (oldest first, at most cap) and forgets
- * them.  Returns the count written.
+ * each call since the option was set (oldest first, at most cap; from the
+ * first class launch to the end of the last, concurrent classes included) and
+ * forgets them.  Returns the count written.
  */
 int32_t fse_context_kernel_times(fse_context_t* ctx, float* ms, int32_t cap);
 
 /*
+ * fse_context_class_times -- as fse_context_kernel_times, per work class and
+ * without forgetting: for each timed call (oldest first, at most cap) three
+ * floats, the milliseconds of the class's own launch (0: FP32 F = 32,
+ * 1: FP32 F = 64, 2: FP64; 0 when the call had no such work).  ms holds
+ * 3 * cap floats.  Returns the number of calls written.
+ */
+int32_t fse_context_class_times(fse_context_t* ctx, float* ms, int32_t cap);
+
+/*
  * fse_autotune -- times the given job mix (device pointers, as for
  * fse_extrapolate_batch; the outputs are written) under candidate launch
- * configurations of each work class present: for F = 64 the executor layout
- * (FSE_OPT_F64_WARPS 6, 4, 5, 2, 8) and the persistent CTAs per SM, for F = 32
- * the layout (FSE_OPT_F32_LAYOUT 3, 1, 2) and the CTAs per SM.  Each candidate
- * runs `reps` times (median of the iteration-kernel time); the fastest is
- * applied to the context and, when the context has a tune cache path, written
- * there.  The layouts are process-wide settings.  Writes up to cap results as (class, layout,
- * ctas_per_sm, milliseconds) quadruples into `trace` (may be NULL) and
- * returns how many candidates ran, or a negative status.
+ * configurations of each work class present: the executor layout
+ * (FSE_OPT_F64_WARPS 6, 4, 5, 2, 8; FSE_OPT_F32_LAYOUT 3, 2, 1), the K-loop
+ * unroll factor (1, 2 where the layout has it) and the persistent CTAs per
+ * SM; then, for a mix of classes, the class launch (FSE_OPT_CLASS_LAUNCH 0, 1,
+ * 2).  Each candidate runs `reps` times (median of the iteration-kernel time);
+ * the fastest is applied to this context only and, when the context has a tune
+ * cache path, written there.  Writes up to cap results as quadruples into
+ * `trace` (may be NULL): (class, layout * 10 + unroll, ctas_per_sm, ms) for the
+ * class candidates and (-1, launch mode, 0, ms) for the class launches.
+ * Returns how many candidates ran, or a negative status.
  */
 int32_t fse_autotune(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void* cuda_stream,
                      int32_t reps, double* trace, int32_t cap);

@@ -21,6 +21,7 @@ ORDER = {"phased": 0, "raster": 1, "independent": 2}
 TILING = {"alg1": 0, "vertical": 1}
 OPT_EXEC_MODE, OPT_TIMEOUT_MS, OPT_CTAS_PER_SM, OPT_USE_GRAPH, OPT_DEBUG_CAPTURE, OPT_KERNEL_TIMING = 1, 2, 3, 4, 5, 6
 OPT_F64_WARPS, OPT_F32_LAYOUT, OPT_TMA_STAGING, OPT_DEBUG_TMA_STALL = 7, 8, 9, 10
+OPT_F32_UNROLL, OPT_F64_UNROLL, OPT_CLASS_LAUNCH = 11, 12, 13
 EXEC = {"dag": 0, "levels": 1, "per_block": 2}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
@@ -55,10 +56,14 @@ class Stats(ctypes.Structure):
                 ("bin_iterations", ctypes.c_int64), ("jobs", ctypes.c_int32),
                 ("tiles", ctypes.c_int32), ("launches", ctypes.c_int32),
                 ("graph_replayed", ctypes.c_int32), ("device_ms", ctypes.c_float),
-                ("exec_ms", ctypes.c_float)]
+                ("exec_ms", ctypes.c_float), ("class_blocks", ctypes.c_int64 * 3),
+                ("class_bin_iterations", ctypes.c_int64 * 3)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        d = {n: getattr(self, n) for n, _ in self._fields_}
+        for n in ("class_blocks", "class_bin_iterations"):
+            d[n] = list(d[n])
+        return d
 
 
 class ServerCfg(ctypes.Structure):
@@ -70,7 +75,7 @@ EXPORTS = ["fse_plan_tiles", "fse_plan_tiles_vertical", "fse_context_create", "f
            "fse_extrapolate_batch", "fse_extrapolate_host", "fse_server_create", "fse_submit",
            "fse_poll", "fse_wait", "fse_server_latencies", "fse_server_destroy", "fse_last_error",
            "fse_debug_fetch", "fse_debug_wait_probe", "fse_context_kernel_times",
-           "fse_extrapolate_noalloc", "fse_autotune"]
+           "fse_extrapolate_noalloc", "fse_autotune", "fse_context_class_times"]
 
 _lib = None
 
@@ -109,6 +114,8 @@ def load(path=LIB_PATH):
     L.fse_autotune.restype = i32
     L.fse_context_kernel_times.argtypes = [vp, P(ctypes.c_float), i32]
     L.fse_context_kernel_times.restype = i32
+    L.fse_context_class_times.argtypes = [vp, P(ctypes.c_float), i32]
+    L.fse_context_class_times.restype = i32
     _lib = L
     return L
 
@@ -237,6 +244,13 @@ class Context:
         ms = (ctypes.c_float * cap)()
         n = _check(load().fse_context_kernel_times(self.h, ms, cap))
         return [ms[i] for i in range(n)]
+
+    def class_times(self, cap=4096):
+        """Per-class iteration-kernel milliseconds [[F=32, F=64, FP64], ...] of
+        each timed call (does not forget them; kernel_times does)."""
+        ms = (ctypes.c_float * (3 * cap))()
+        n = _check(load().fse_context_class_times(self.h, ms, cap))
+        return [[ms[3 * i + k] for k in range(3)] for i in range(n)]
 
     def wait_probe(self, timeout_us):
         return load().fse_debug_wait_probe(self.h, timeout_us)

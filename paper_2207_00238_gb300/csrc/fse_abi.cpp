@@ -18,9 +18,8 @@ using fse::Context;
 namespace fse {
 
 // Autotuner cache: the GPU name on the first line, then one line per work
-// class "cls ctas_per_sm layout" (layout: FSE_OPT_F32_LAYOUT for class 0,
-// FSE_OPT_F64_WARPS for class 1).
-// A missing or foreign file is ignored.
+// class "cls ctas_per_sm layout unroll" and one line "order concurrent order"
+// for the class launches.  A missing or foreign file is ignored.
 void tune_load(Context* c) {
   FILE* f = fopen(c->tune_path.c_str(), "r");
   if (!f) return;
@@ -30,12 +29,19 @@ void tune_load(Context* c) {
   if (fgets(name, sizeof(name), f)) {
     name[strcspn(name, "\r\n")] = 0;
     if (strcmp(name, prop.name) == 0) {
-      int k, v, lay;
-      while (fscanf(f, "%d %d %d", &k, &v, &lay) == 3) {
-        if (k < 0 || k >= MAX_CLS || v <= 0) continue;
+      char line[256];
+      while (fgets(line, sizeof(line), f)) {
+        int k, v, lay, un;
+        if (sscanf(line, "order %d %d", &v, &lay) == 2) {
+          c->concurrent = v != 0;
+          c->class_order = lay == 1;
+          continue;
+        }
+        if (sscanf(line, "%d %d %d %d", &k, &v, &lay, &un) != 4) continue;
+        if (k < 0 || k >= MAX_CLS || v <= 0 || !exec_cfg_valid(k, k == CLS_F64 ? 0 : lay, un)) continue;
         c->tuned_ctas[k] = v;
-        if (k == CLS_F32_64 && (lay == 2 || lay == 4 || lay == 5 || lay == 6 || lay == 8)) set_f64_warps(lay);
-        if (k == CLS_F32_32 && lay >= 1 && lay <= 3) set_f32_layout(lay);
+        if (k == CLS_F32_32) { c->cfg.lay32 = lay; c->cfg.unroll32 = un; }
+        if (k == CLS_F32_64) { c->cfg.lay64 = lay; c->cfg.unroll64 = un; }
       }
     }
   }
@@ -50,15 +56,12 @@ static void tune_save(Context* c) {
   cudaGetDeviceProperties(&prop, c->device);
   fprintf(f, "%s\n", prop.name);
   for (int k = 0; k < MAX_CLS; ++k)
-    if (c->tuned_ctas[k] > 0) fprintf(f, "%d %d %d\n", k, c->tuned_ctas[k], k == CLS_F32_64 ? get_f64_warps() : (k == CLS_F32_32 ? get_f32_layout() : 0));
+    if (c->tuned_ctas[k] > 0)
+      fprintf(f, "%d %d %d %d\n", k, c->tuned_ctas[k],
+              k == CLS_F32_64 ? c->cfg.lay64 : (k == CLS_F32_32 ? c->cfg.lay32 : 0),
+              k == CLS_F32_64 ? c->cfg.unroll64 : (k == CLS_F32_32 ? c->cfg.unroll32 : 1));
+  fprintf(f, "order %d %d\n", c->concurrent, c->class_order);
   fclose(f);
-}
-
-static int occupancy_of(int cls) {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(cls), exec_threads(cls),
-                                                exec_smem(cls));
-  return nb > 0 ? nb : 1;
 }
 
 int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int reps,
@@ -75,20 +78,22 @@ int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int 
   c->exec_mode = FSE_EXEC_DAG;
   c->use_graph = 0;
   int ran = 0;
-  auto time_cfg = [&](int cls, int layout, int ctas, double* ms_out) -> int {
-    c->ctas_per_sm = ctas;
+  // median iteration-kernel time of `reps` runs after one warm-up; trace rows
+  // (class or -1 for the class launch order, layout*10 + unroll or order code,
+  // ctas per SM, milliseconds)
+  auto time_cfg = [&](int cls, int code, int ctas, double* ms_out) -> int {
     std::vector<double> ms;
     for (int r = 0; r < reps + 1; ++r) {
       fse_stats_t stt;
       int rc = run_batch(c, jobs, n, st, &stt, 0);
       if (rc) return rc;
-      if (r > 0) ms.push_back(stt.exec_ms);  // first run warms up
+      if (r > 0) ms.push_back(stt.exec_ms);
     }
     std::sort(ms.begin(), ms.end());
     *ms_out = ms[ms.size() / 2];
     if (trace && ran < cap) {
       trace[4 * ran] = cls;
-      trace[4 * ran + 1] = layout;
+      trace[4 * ran + 1] = code;
       trace[4 * ran + 2] = ctas;
       trace[4 * ran + 3] = *ms_out;
     }
@@ -96,55 +101,67 @@ int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int 
     return FSE_OK;
   };
   int rc = FSE_OK;
-  // F = 64: executor layout x CTAs per SM (only this class is timed; the
-  // others run at their current setting and add a constant)
-  if (present[CLS_F32_64]) {
+  // per class: executor layout x K-loop unroll x persistent CTAs per SM, with
+  // the classes launched one after the other (the other classes run at their
+  // current setting and add a constant)
+  const int saved_conc = c->concurrent;
+  c->concurrent = 0;
+  struct Cand { int lay, un, ctas_span; };
+  const Cand cand64[] = {{6, 1, 1}, {6, 2, 1}, {4, 1, 1}, {5, 1, 1}, {2, 1, 1}, {8, 1, 1}};
+  const Cand cand32[] = {{3, 1, 3}, {3, 2, 3}, {2, 1, 3}, {2, 2, 3}, {1, 1, 3}};
+  for (int cls : {CLS_F32_64, CLS_F32_32}) {
+    if (!present[cls] || rc != FSE_OK) continue;
+    const Cand* cands = cls == CLS_F32_64 ? cand64 : cand32;
+    const int ncand = cls == CLS_F32_64 ? 6 : 5;
+    int& lay = cls == CLS_F32_64 ? c->cfg.lay64 : c->cfg.lay32;
+    int& un = cls == CLS_F32_64 ? c->cfg.unroll64 : c->cfg.unroll32;
     double best = 1e30;
-    int best_lay = get_f64_warps(), best_ctas = 0;
-    const int layouts[5] = {6, 4, 5, 2, 8};
-    for (int li = 0; li < 5 && rc == FSE_OK; ++li) {
-      set_f64_warps(layouts[li]);
-      c->occupancy[CLS_F32_64] = occupancy_of(CLS_F32_64);
-      const int occ = c->occupancy[CLS_F32_64];
-      for (int k = occ; k >= 1 && k >= occ - 1 && rc == FSE_OK; --k) {
+    int best_lay = lay, best_un = un, best_ctas = 0;
+    for (int ci = 0; ci < ncand && rc == FSE_OK; ++ci) {
+      lay = cands[ci].lay;
+      un = cands[ci].un;
+      update_occupancy(c);
+      const int occ = c->occupancy[cls];
+      for (int k = occ; k >= 1 && k >= occ - cands[ci].ctas_span && rc == FSE_OK; --k) {
+        c->ctas_per_sm = k;
         double ms;
-        rc = time_cfg(CLS_F32_64, layouts[li], k, &ms);
+        rc = time_cfg(cls, lay * 10 + un, k, &ms);
         if (rc == FSE_OK && ms < best) {
           best = ms;
-          best_lay = layouts[li];
+          best_lay = lay;
+          best_un = un;
           best_ctas = k;
         }
       }
     }
-    set_f64_warps(best_lay);
-    c->occupancy[CLS_F32_64] = occupancy_of(CLS_F32_64);
-    c->tuned_ctas[CLS_F32_64] = best_ctas;
+    lay = best_lay;
+    un = best_un;
+    update_occupancy(c);
+    c->tuned_ctas[cls] = best_ctas;
   }
-  if (present[CLS_F32_32] && rc == FSE_OK) {
+  c->ctas_per_sm = saved_ctas;
+  c->concurrent = saved_conc;
+  // class launches of a mixed call: one after the other, or concurrent on
+  // forked streams with either class first (order code 0: sequential,
+  // 1: concurrent F = 64 first, 2: concurrent F = 32 first)
+  if (rc == FSE_OK && present[CLS_F32_32] + present[CLS_F32_64] + present[CLS_F64] > 1) {
     double best = 1e30;
-    int best_lay = get_f32_layout(), best_ctas = 0;
-    const int layouts[3] = {3, 1, 2};
-    for (int li = 0; li < 3 && rc == FSE_OK; ++li) {
-      set_f32_layout(layouts[li]);
-      c->occupancy[CLS_F32_32] = occupancy_of(CLS_F32_32);
-      const int occ = c->occupancy[CLS_F32_32];
-      for (int k = occ; k >= 1 && k >= occ - 3 && rc == FSE_OK; --k) {
-        double ms;
-        rc = time_cfg(CLS_F32_32, layouts[li], k, &ms);
-        if (rc == FSE_OK && ms < best) {
-          best = ms;
-          best_lay = layouts[li];
-          best_ctas = k;
-        }
+    int best_code = 0;
+    for (int code = 0; code < 3 && rc == FSE_OK; ++code) {
+      c->concurrent = code != 0;
+      c->class_order = code == 2;
+      double ms;
+      rc = time_cfg(-1, code, 0, &ms);
+      if (rc == FSE_OK && ms < best) {
+        best = ms;
+        best_code = code;
       }
     }
-    set_f32_layout(best_lay);
-    c->occupancy[CLS_F32_32] = occupancy_of(CLS_F32_32);
-    c->tuned_ctas[CLS_F32_32] = best_ctas;
+    c->concurrent = best_code != 0;
+    c->class_order = best_code == 2;
   }
   c->exec_mode = saved_mode;
   c->use_graph = saved_graph;
-  c->ctas_per_sm = saved_ctas;
   c->graph_jobs.clear();
   if (rc) return rc;
   tune_save(c);
@@ -269,28 +286,37 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       c->graph_jobs.clear();
       return FSE_OK;
     case FSE_OPT_F32_LAYOUT: {
+      const int lay = value == 0 ? 3 : (int)value;
       if (value < 0 || value > 3) return fse::fail(FSE_EINVAL, "f32 layout");
-      fse::set_f32_layout(value == 0 ? 3 : (int)value);
-      int nb = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fse::exec_kernel_ptr(fse::CLS_F32_32),
-                                                    fse::exec_threads(fse::CLS_F32_32),
-                                                    fse::exec_smem(fse::CLS_F32_32));
-      c->occupancy[fse::CLS_F32_32] = nb > 0 ? nb : 1;
-      c->graph_jobs.clear();
+      c->cfg.lay32 = lay;
+      if (!fse::exec_cfg_valid(fse::CLS_F32_32, lay, c->cfg.unroll32)) c->cfg.unroll32 = 1;
+      fse::update_occupancy(c);
       return FSE_OK;
     }
     case FSE_OPT_F64_WARPS: {
-      if (value != 0 && value != 2 && value != 4 && value != 5 && value != 6 && value != 8)
-        return fse::fail(FSE_EINVAL, "f64 warps");
-      fse::set_f64_warps(value == 0 ? 6 : (int)value);
-      int nb = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fse::exec_kernel_ptr(fse::CLS_F32_64),
-                                                    fse::exec_threads(fse::CLS_F32_64),
-                                                    fse::exec_smem(fse::CLS_F32_64));
-      c->occupancy[fse::CLS_F32_64] = nb > 0 ? nb : 1;
-      c->graph_jobs.clear();
+      const int lay = value == 0 ? 6 : (int)value;
+      if (!fse::exec_cfg_valid(fse::CLS_F32_64, lay, 1)) return fse::fail(FSE_EINVAL, "f64 warps");
+      c->cfg.lay64 = lay;
+      if (!fse::exec_cfg_valid(fse::CLS_F32_64, lay, c->cfg.unroll64)) c->cfg.unroll64 = 1;
+      fse::update_occupancy(c);
       return FSE_OK;
     }
+    case FSE_OPT_F32_UNROLL:
+    case FSE_OPT_F64_UNROLL: {
+      const int cls = key == FSE_OPT_F32_UNROLL ? fse::CLS_F32_32 : fse::CLS_F32_64;
+      const int un = value == 0 ? 1 : (int)value;
+      const int lay = cls == fse::CLS_F32_32 ? c->cfg.lay32 : c->cfg.lay64;
+      if (!fse::exec_cfg_valid(cls, lay, un)) return fse::fail(FSE_EINVAL, "unroll %d for layout %d", un, lay);
+      (cls == fse::CLS_F32_32 ? c->cfg.unroll32 : c->cfg.unroll64) = un;
+      fse::update_occupancy(c);
+      return FSE_OK;
+    }
+    case FSE_OPT_CLASS_LAUNCH:
+      if (value < 0 || value > 2) return fse::fail(FSE_EINVAL, "class launch %d", (int)value);
+      c->concurrent = value != 0;
+      c->class_order = value == 2;
+      c->graph_jobs.clear();
+      return FSE_OK;
     case FSE_OPT_DEBUG_TMA_STALL:
       c->dbg_tma_stall = value != 0;
       c->graph_jobs.clear();
@@ -298,6 +324,7 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
     case FSE_OPT_KERNEL_TIMING:
       c->kernel_timing = value != 0;
       c->tev_used = 0;
+      c->tev_cls_mask.clear();
       return FSE_OK;
     default:
       return fse::fail(FSE_EINVAL, "unknown option %d", key);
@@ -326,18 +353,42 @@ int32_t fse_autotune(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void*
   return fse::autotune(ctx, jobs, n, (cudaStream_t)cuda_stream, reps, trace, cap);
 }
 
+// Timed calls store 2 + 2 * MAX_CLS events each: start and end of the whole
+// execution, then start and end per class.
+static constexpr size_t kEventsPerCall = 2 + 2 * fse::MAX_CLS;
+
+int32_t fse_context_class_times(fse_context_t* c, float* ms, int32_t cap) {
+  if (!c || (!ms && cap > 0)) return fse::fail(FSE_EINVAL, "NULL argument");
+  if (cudaSetDevice(c->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return fse::fail(FSE_ECUDA, "synchronize");
+  int32_t n = 0;
+  for (size_t call = 0; (call + 1) * kEventsPerCall <= c->tev_used && n < cap; ++call, ++n) {
+    const cudaEvent_t* e = &c->tev[call * kEventsPerCall];
+    for (int k = 0; k < fse::MAX_CLS; ++k) {
+      float v = 0;
+      if ((c->tev_cls_mask[call] >> k) & 1)
+        if (cudaEventElapsedTime(&v, e[2 + 2 * k], e[3 + 2 * k]) != cudaSuccess)
+          return fse::fail(FSE_ECUDA, "cudaEventElapsedTime");
+      ms[(size_t)n * fse::MAX_CLS + k] = v;
+    }
+  }
+  return n;
+}
+
 int32_t fse_context_kernel_times(fse_context_t* c, float* ms, int32_t cap) {
   if (!c || (!ms && cap > 0)) return fse::fail(FSE_EINVAL, "NULL argument");
   if (cudaSetDevice(c->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
     return fse::fail(FSE_ECUDA, "synchronize");
   int32_t n = 0;
-  for (size_t i = 0; i + 1 < c->tev_used && n < cap; i += 2) {
+  for (size_t call = 0; (call + 1) * kEventsPerCall <= c->tev_used && n < cap; ++call) {
     float v = 0;
-    if (cudaEventElapsedTime(&v, c->tev[i], c->tev[i + 1]) != cudaSuccess)
+    if (cudaEventElapsedTime(&v, c->tev[call * kEventsPerCall], c->tev[call * kEventsPerCall + 1]) !=
+        cudaSuccess)
       return fse::fail(FSE_ECUDA, "cudaEventElapsedTime");
     ms[n++] = v;
   }
   c->tev_used = 0;
+  c->tev_cls_mask.clear();
   return n;
 }
 

@@ -195,26 +195,32 @@ static int context_init(Context** out, int device, size_t arena_bytes, char* ali
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev2);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev3);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < MAX_CLS && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&c->cls_stream[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     context_destroy(c);
     return cuda_fail(e, "context setup");
   }
-  for (int k = 0; k < MAX_CLS; ++k) {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(k), exec_threads(k), exec_smem(k));
-    c->occupancy[k] = std::max(1, nb);
-  }
   if (tune_path) {
     c->tune_path = tune_path;
     tune_load(c);
-    for (int k = 0; k < MAX_CLS; ++k) {  // the cache may have changed a layout
-      int nb = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(k), exec_threads(k), exec_smem(k));
-      c->occupancy[k] = std::max(1, nb);
-    }
   }
+  update_occupancy(c);
   *out = c;
   return FSE_OK;
+}
+
+void update_occupancy(Context* c) {
+  for (int k = 0; k < MAX_CLS; ++k) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(k, c->cfg), exec_threads(k, c->cfg),
+                                                  exec_smem(k, c->cfg));
+    c->occupancy[k] = std::max(1, nb);
+  }
+  c->graph_jobs.clear();  // a captured graph holds the old variants
 }
 
 int context_create(Context** out, int device, size_t arena_bytes, const char* tune_path) {
@@ -237,6 +243,11 @@ void context_destroy(Context* c) {
   if (c->ev3) cudaEventDestroy(c->ev3);
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  for (int k = 0; k < MAX_CLS; ++k) {
+    if (c->cls_stream[k]) cudaStreamDestroy(c->cls_stream[k]);
+    if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+  }
   delete c;
 }
 
@@ -402,7 +413,7 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
   // load/store queue, which pays only when many blocks share each SM, so they
   // are used when the F = 32 class has at least four blocks per resident warp
   if (c->tma == 2 &&
-      P.cap[CLS_F32_32] < 4ll * exec_grid(c, CLS_F32_32) * (exec_threads(CLS_F32_32) / 32))
+      P.cap[CLS_F32_32] < 4ll * exec_grid(c, CLS_F32_32) * (exec_threads(CLS_F32_32, c->cfg) / 32))
     for (JobDev& J : P.jobs) J.tma = 0;
   // arena layout (bytes from the arena base + arena_offset)
   size_t o = arena_offset;
@@ -518,25 +529,51 @@ static int enqueue(Context* c, const Plan& P, const ExecArgs& a, cudaStream_t st
       ++launches;
     }
   if (timed) FSE_CUDA(cudaEventRecord(c->ev2, st));
-  cudaEvent_t k0 = nullptr, k1 = nullptr;
+  // kernel-timing events of this call: start, end, then start / end per class
+  cudaEvent_t* kt = nullptr;
   if (c->kernel_timing && !c->capturing) {
-    if (c->tev_used + 2 > c->tev.size()) {
-      for (int i = 0; i < 64; ++i) {
-        cudaEvent_t e;
-        FSE_CUDA(cudaEventCreate(&e));
-        c->tev.push_back(e);
-      }
+    constexpr size_t per_call = 2 + 2 * MAX_CLS;
+    while (c->tev_used + per_call > c->tev.size()) {
+      cudaEvent_t e;
+      FSE_CUDA(cudaEventCreate(&e));
+      c->tev.push_back(e);
     }
-    k0 = c->tev[c->tev_used++];
-    k1 = c->tev[c->tev_used++];
-    FSE_CUDA(cudaEventRecord(k0, st));
+    kt = &c->tev[c->tev_used];
+    c->tev_used += per_call;
+    int mask = 0;
+    for (int k = 0; k < MAX_CLS; ++k) mask |= P.cap[k] > 0 ? 1 << k : 0;
+    c->tev_cls_mask.push_back(mask);
+    FSE_CUDA(cudaEventRecord(kt[0], st));
   }
   if (c->exec_mode == FSE_EXEC_DAG) {
+    // One persistent launch per work class.  With several classes they run
+    // concurrently on forked streams (joined back into st, so a captured graph
+    // holds them as parallel nodes): the persistent CTAs of the class launched
+    // first fill the GPU, and as they drain, the next class's CTAs take the
+    // freed SMs, so each class's dependency tail overlaps the other's work.
+    int order[MAX_CLS] = {CLS_F32_64, CLS_F32_32, CLS_F64};
+    if (c->class_order == 1) std::swap(order[0], order[1]);
+    int n_present = 0;
+    for (int k = 0; k < MAX_CLS; ++k) n_present += P.cap[k] > 0;
+    const bool fork = c->concurrent && n_present > 1;
+    if (fork) FSE_CUDA(cudaEventRecord(c->ev_fork, st));
+    bool forked[MAX_CLS] = {false, false, false};
+    bool first = true;
+    for (int oi = 0; oi < MAX_CLS; ++oi) {
+      const int k = order[oi];
+      if (P.cap[k] == 0) continue;
+      forked[k] = fork && !first;  // the first class runs on st itself
+      cudaStream_t sk = forked[k] ? c->cls_stream[k] : st;
+      if (forked[k]) FSE_CUDA(cudaStreamWaitEvent(sk, c->ev_fork, 0));
+      if (kt) FSE_CUDA(cudaEventRecord(kt[2 + 2 * k], sk));
+      FSE_CUDA(launch_exec(a, k, exec_grid(c, k), sk, c->cfg));
+      if (kt) FSE_CUDA(cudaEventRecord(kt[3 + 2 * k], sk));
+      if (forked[k]) FSE_CUDA(cudaEventRecord(c->ev_join[k], sk));
+      ++launches;
+      first = false;
+    }
     for (int k = 0; k < MAX_CLS; ++k)
-      if (P.cap[k] > 0) {
-        FSE_CUDA(launch_exec(a, k, exec_grid(c, k), st));
-        ++launches;
-      }
+      if (forked[k]) FSE_CUDA(cudaStreamWaitEvent(st, c->ev_join[k], 0));
   } else if (c->exec_mode == FSE_EXEC_LEVELS) {
     int max_levels = 1;
     for (const JobDev& J : P.jobs)
@@ -547,12 +584,14 @@ static int enqueue(Context* c, const Plan& P, const ExecArgs& a, cudaStream_t st
           ExecArgs b = a;
           b.level_mode = 1;
           b.level = lv;
-          FSE_CUDA(launch_exec(b, k, exec_grid(c, k), st));
+          if (kt && lv == 0) FSE_CUDA(cudaEventRecord(kt[2 + 2 * k], st));
+          FSE_CUDA(launch_exec(b, k, exec_grid(c, k), st, c->cfg));
+          if (kt) FSE_CUDA(cudaEventRecord(kt[3 + 2 * k], st));
           ++launches;
         }
   }
   if (timed) FSE_CUDA(cudaEventRecord(c->ev3, st));
-  if (k1) FSE_CUDA(cudaEventRecord(k1, st));
+  if (kt) FSE_CUDA(cudaEventRecord(kt[1], st));
   *nl = launches;
   return FSE_OK;
 }
@@ -587,7 +626,7 @@ static int run_per_block(Context* c, const Plan& P, const ExecArgs& a, cudaStrea
   for (const Ent& e : ents) {
     ExecArgs b = a;
     b.single_item = e.id;
-    FSE_CUDA(launch_exec(b, e.cls, 1, st));
+    FSE_CUDA(launch_exec(b, e.cls, 1, st, c->cfg));
   }
   *nl += (int)ents.size();
   return FSE_OK;
@@ -698,8 +737,11 @@ int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse
       else if (kf[J.cls] != v) uniform[J.cls] = false;
     }
     for (int k = 0; k < MAX_CLS; ++k) per_cls[k] = kf[k] < 0 ? 0 : kf[k];
-    for (int k = 0; k < MAX_CLS; ++k)
+    for (int k = 0; k < MAX_CLS; ++k) {
+      stats->class_blocks[k] = q[k].n_items;
+      stats->class_bin_iterations[k] = uniform[k] ? per_cls[k] * (q[k].n_items - q[k].n_empty) : -1;
       stats->bin_iterations += uniform[k] ? per_cls[k] * (q[k].n_items - q[k].n_empty) : -1;
+    }
     if (stats->bin_iterations < 0) stats->bin_iterations = -1;
   }
   cudaEventElapsedTime(&stats->device_ms, c->ev0, c->ev1);

@@ -32,7 +32,14 @@ struct fse_context {
   int dbg_tma_stall = 0;  // test only (FSE_OPT_DEBUG_TMA_STALL)
   std::vector<cudaEvent_t> tev;  // pairs: start, end of the iteration kernels
   size_t tev_used = 0;
-  int occupancy[fse::MAX_CLS] = {1, 1, 1};
+  fse::ExecCfg cfg;                    // executor variant per class (options, autotuner)
+  int occupancy[fse::MAX_CLS] = {1, 1, 1};  // of cfg's variants
+  int concurrent = 1;                  // work classes of one call run on forked streams
+  int class_order = 0;                 // 0: F = 64 class launched first; 1: F = 32 first
+  cudaStream_t cls_stream[fse::MAX_CLS] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[fse::MAX_CLS] = {nullptr, nullptr, nullptr};
+  // per timed call: start/end of the whole execution, then start/end per class
+  std::vector<int> tev_cls_mask;
   std::string tune_path;
   int tuned_ctas[fse::MAX_CLS] = {0, 0, 0};
   // cached graph of the last job set
@@ -68,6 +75,7 @@ void context_destroy(Context* c);
 int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse_stats_t* stats,
               size_t arena_offset);
 int exec_grid(Context* c, int cls);
+void update_occupancy(Context* c);  // occupancy of the context's variants
 void tune_load(Context* c);
 int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int reps, double* trace,
              int cap);

@@ -102,21 +102,30 @@ struct ExecArgs {
   int64_t level_stride;
 };
 
+// Executor configuration of one context: which kernel variant runs each work
+// class.  F = 32 layouts: 1 one spectrum column per lane, 2 paired bins, 3 row
+// runs; F = 64 layouts: 2, 4, 8 warps per block, 5 four warps with a 96-row
+// table, 6 four warps with paired bins.  unroll: K-loop unroll factor (1 or 2;
+// 2 exists for layouts 2, 3 and 6).
+struct ExecCfg {
+  int32_t lay32 = 3;
+  int32_t lay64 = 6;
+  int32_t unroll32 = 1;
+  int32_t unroll64 = 1;
+};
+
 // Launch wrappers (fse_kernels.cu).  All are stream-ordered, none syncs.
 void set_twiddles(const float2* tw_f, const double2* tw_d);  // 64 entries each
 cudaError_t launch_init_out(const JobDev* jobs_dev, int n_jobs, int max_pixels,
                             cudaStream_t st);
 cudaError_t launch_mark(const ExecArgs& a, int n_tiles, int max_tile_blocks, cudaStream_t st);
 cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st);
-cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st);
+cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st, const ExecCfg& cfg);
 cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st);
-int exec_threads(int cls);
-void set_f64_warps(int nwb);  // warps per block of the F = 64 executor (4 or 8)
-int get_f64_warps();
-void set_f32_layout(int lay);  // F = 32 executor: 1 = one column per lane, 2 = paired bins, 3 = row runs
-int get_f32_layout();
-size_t exec_smem(int cls);
+bool exec_cfg_valid(int cls, int layout, int unroll);  // a kernel variant exists
+int exec_threads(int cls, const ExecCfg& cfg);
+size_t exec_smem(int cls, const ExecCfg& cfg);
+const void* exec_kernel_ptr(int cls, const ExecCfg& cfg);
 cudaError_t exec_setup(int device);  // smem opt-in for every executor kernel
-const void* exec_kernel_ptr(int cls);
 
 }  // namespace fse

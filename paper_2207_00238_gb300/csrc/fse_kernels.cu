@@ -930,6 +930,7 @@ struct alignas(128) WarpSmem32P {
   JobDev J;
 };
 
+template <int U>
 __device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem32P& sm, const float2* tw,
                                              int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
@@ -1002,6 +1003,7 @@ __device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem
                        make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
   });
   uint32_t best = max(bq[0], bq[1]);
+#pragma unroll U  // K-loop unroll factor (autotuned)
   for (int iter = 0; iter < K; ++iter) {
     const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
     const int l_w = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
@@ -1072,6 +1074,7 @@ struct alignas(128) WarpSmem32R {
   JobDev J;
 };
 
+template <int U>
 __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WarpSmem32R& sm, const float2* tw,
                                              int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
@@ -1126,6 +1129,7 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WarpSmem
                              make_key<30u - j>(e1, kmask));
   });
   uint32_t best = max(bq[0], bq[1]);
+#pragma unroll U  // K-loop unroll factor (autotuned)
   for (int iter = 0; iter < K; ++iter) {
     const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
     const int u2 = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
@@ -1171,14 +1175,14 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WarpSmem
 }
 constexpr size_t SMEM32R = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32R);
 
-template <class WS>
+template <class WS, int U>
 __device__ __forceinline__ bool run_item32(const ExecArgs& a, int id, WS& sm, const float2* tw, int lane) {
-  if constexpr (std::is_same<WS, WarpSmem32P>::value) return item_f32_32p(a, id, sm, tw, lane);
-  else if constexpr (std::is_same<WS, WarpSmem32R>::value) return item_f32_32r(a, id, sm, tw, lane);
+  if constexpr (std::is_same<WS, WarpSmem32P>::value) return item_f32_32p<U>(a, id, sm, tw, lane);
+  else if constexpr (std::is_same<WS, WarpSmem32R>::value) return item_f32_32r<U>(a, id, sm, tw, lane);
   else return item_f32_32(a, id, sm, tw, lane);
 }
 
-template <class WS>
+template <class WS, int U>
 __global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32R>::value ? 6 : 5)
     k_exec_f32_32(const __grid_constant__ ExecArgs a) {
   extern __shared__ __align__(128) unsigned char smem32_raw[];
@@ -1195,20 +1199,20 @@ __global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32R>::valu
   __syncwarp();
   const ClassArgs& C = a.c[CLS_F32_32];
   if (a.single_item >= 0) {
-    if (blockIdx.x == 0 && warp == 0) run_item32(a, a.single_item, sm, tw, lane);
+    if (blockIdx.x == 0 && warp == 0) run_item32<WS, U>(a, a.single_item, sm, tw, lane);
     return;
   }
   if (a.level_mode) {
     const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x * NW32 + warp; id < n; id += gridDim.x * NW32)
       if (a.level_of[(size_t)CLS_F32_32 * a.level_stride + id] == a.level)
-        if (!run_item32(a, id, sm, tw, lane)) break;
+        if (!run_item32<WS, U>(a, id, sm, tw, lane)) break;
     return;
   }
   for (;;) {
     const int id = queue_pop_warp(C, a.timeout_ns, lane);
     if (id < 0) break;
-    if (!run_item32(a, id, sm, tw, lane)) break;  // staging timed out: this warp stops
+    if (!run_item32<WS, U>(a, id, sm, tw, lane)) break;  // staging timed out: this warp stops
     // value-plane stores before later blocks' TMA (asynchronous-proxy) reads
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __threadfence();
@@ -1463,7 +1467,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
 // ---------------------------------------------------------------------------
 constexpr int ROWS_PAIRED = 134;  // 67 rows of 64 float4 slots, counted in float2 rows
 
-template <int NWB, int ROWS>
+template <int NWB, int ROWS, int U>
 __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
   static_assert(NWB == 4 && ROWS == ROWS_PAIRED, "paired layout: 4 warps, 67 table rows");
   constexpr int NT = 128;
@@ -1537,6 +1541,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
                        make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
   });
   uint32_t best = max(bq[0], bq[1]);
+#pragma unroll U  // K-loop unroll factor (autotuned)
   for (int iter = 0; iter < K; ++iter) {
     {
       const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
@@ -1598,13 +1603,13 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
                                       NT);
 }
 
-template <int NWB, int ROWS>
+template <int NWB, int ROWS, int U>
 __device__ __forceinline__ void run_item64(const ExecArgs& a, int id, CtaSmem64<NWB, ROWS>& sm, int t) {
-  if constexpr (ROWS == ROWS_PAIRED) item_f32_64p<NWB, ROWS>(a, id, sm, t);
+  if constexpr (ROWS == ROWS_PAIRED) item_f32_64p<NWB, ROWS, U>(a, id, sm, t);
   else item_f32_64<NWB, ROWS>(a, id, sm, t);
 }
 
-template <int NWB, int ROWS = 128>
+template <int NWB, int ROWS = 128, int U = 1>
 __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS == 96 ? 4 : 3)))
     k_exec_f32_64(const __grid_constant__ ExecArgs a) {
   constexpr int NT = NWB * 32;
@@ -1615,14 +1620,14 @@ __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS
   __syncthreads();
   const ClassArgs& C = a.c[CLS_F32_64];
   if (a.single_item >= 0) {
-    if (blockIdx.x == 0) run_item64<NWB, ROWS>(a, a.single_item, sm, t);
+    if (blockIdx.x == 0) run_item64<NWB, ROWS, U>(a, a.single_item, sm, t);
     return;
   }
   if (a.level_mode) {
     const int n = min(C.q->n_items, C.cap);
     for (int id = blockIdx.x; id < n; id += gridDim.x)
       if (a.level_of[(size_t)CLS_F32_64 * a.level_stride + id] == a.level) {
-        run_item64<NWB, ROWS>(a, id, sm, t);
+        run_item64<NWB, ROWS, U>(a, id, sm, t);
         __syncthreads();
       }
     return;
@@ -1635,7 +1640,7 @@ __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS
     __syncthreads();
     const int id = sm.item;
     if (id < 0) break;
-    run_item64<NWB, ROWS>(a, id, sm, t);
+    run_item64<NWB, ROWS, U>(a, id, sm, t);
     __threadfence();
     __syncthreads();
     const int2 it = C.items[id];
@@ -1920,64 +1925,60 @@ __global__ void k_probe(const __grid_constant__ ExecArgs a) {
 // ===========================================================================
 // launchers
 // ===========================================================================
-int g_nwb64 = 6;  // layout of the F = 64 executor (warps per block 2, 4, 8; 5, 6: 4 warps)
-void set_f64_warps(int nwb) { g_nwb64 = (nwb == 8 || nwb == 2 || nwb == 4 || nwb == 5) ? nwb : 6; }
-int get_f64_warps() { return g_nwb64; }
-int g_lay32 = 3;  // layout of the F = 32 executor: 1 = one column per lane, 2 = paired bins, 3 = row runs
-void set_f32_layout(int lay) { g_lay32 = (lay == 1 || lay == 2) ? lay : 3; }
-int get_f32_layout() { return g_lay32; }
-int exec_threads(int cls) {
-  return cls == CLS_F32_32 ? NW32 * 32 : (cls == CLS_F32_64 ? (g_nwb64 == 5 || g_nwb64 == 6 ? 4 : g_nwb64) * 32 : NT64);
+// Executor variants: one kernel per (class, layout, K-loop unroll).
+namespace {
+struct Variant {
+  int cls, layout, unroll;
+  const void* fn;
+  int threads;
+  size_t smem;
+};
+const Variant kVariants[] = {
+    {CLS_F32_32, 3, 1, (const void*)k_exec_f32_32<WarpSmem32R, 1>, NW32 * 32, SMEM32R},
+    {CLS_F32_32, 3, 2, (const void*)k_exec_f32_32<WarpSmem32R, 2>, NW32 * 32, SMEM32R},
+    {CLS_F32_32, 2, 1, (const void*)k_exec_f32_32<WarpSmem32P, 1>, NW32 * 32, SMEM32P},
+    {CLS_F32_32, 2, 2, (const void*)k_exec_f32_32<WarpSmem32P, 2>, NW32 * 32, SMEM32P},
+    {CLS_F32_32, 1, 1, (const void*)k_exec_f32_32<WarpSmem32, 1>, NW32 * 32, SMEM32},
+    {CLS_F32_64, 6, 1, (const void*)k_exec_f32_64<4, ROWS_PAIRED, 1>, 128, sizeof(CtaSmem64<4, ROWS_PAIRED>)},
+    {CLS_F32_64, 6, 2, (const void*)k_exec_f32_64<4, ROWS_PAIRED, 2>, 128, sizeof(CtaSmem64<4, ROWS_PAIRED>)},
+    {CLS_F32_64, 5, 1, (const void*)k_exec_f32_64<4, 96>, 128, sizeof(CtaSmem64<4, 96>)},
+    {CLS_F32_64, 4, 1, (const void*)k_exec_f32_64<4>, 128, sizeof(CtaSmem64<4>)},
+    {CLS_F32_64, 2, 1, (const void*)k_exec_f32_64<2>, 64, sizeof(CtaSmem64<2>)},
+    {CLS_F32_64, 8, 1, (const void*)k_exec_f32_64<8>, 256, sizeof(CtaSmem64<8>)},
+    {CLS_F64, 0, 1, (const void*)k_exec_f64, NT64, SMEMD},
+};
+
+const Variant& variant(int cls, const ExecCfg& c) {
+  const int lay = cls == CLS_F32_32 ? c.lay32 : (cls == CLS_F32_64 ? c.lay64 : 0);
+  const int un = cls == CLS_F32_32 ? c.unroll32 : (cls == CLS_F32_64 ? c.unroll64 : 1);
+  const Variant* fallback = nullptr;
+  for (const Variant& v : kVariants) {
+    if (v.cls != cls) continue;
+    if (!fallback) fallback = &v;  // the first listed is the class default
+    if (v.layout == lay && v.unroll == un) return v;
+  }
+  for (const Variant& v : kVariants)  // an unroll the layout lacks: its unroll-1 form
+    if (v.cls == cls && v.layout == lay && v.unroll == 1) return v;
+  return *fallback;
 }
-size_t exec_smem(int cls) {
-  if (cls == CLS_F32_32) return g_lay32 == 1 ? SMEM32 : (g_lay32 == 2 ? SMEM32P : SMEM32R);
-  if (cls == CLS_F32_64)
-    return g_nwb64 == 8 ? sizeof(CtaSmem64<8>)
-                        : (g_nwb64 == 2 ? sizeof(CtaSmem64<2>)
-                                        : (g_nwb64 == 5 ? sizeof(CtaSmem64<4, 96>)
-                                                        : (g_nwb64 == 6 ? sizeof(CtaSmem64<4, ROWS_PAIRED>)
-                                                                        : sizeof(CtaSmem64<4>))));
-  return SMEMD;
+}  // namespace
+
+bool exec_cfg_valid(int cls, int layout, int unroll) {
+  for (const Variant& v : kVariants)
+    if (v.cls == cls && v.layout == layout && v.unroll == unroll) return true;
+  return false;
 }
-const void* exec_kernel_ptr(int cls) {
-  if (cls == CLS_F32_32)
-    return g_lay32 == 1   ? (const void*)k_exec_f32_32<WarpSmem32>
-           : g_lay32 == 2 ? (const void*)k_exec_f32_32<WarpSmem32P>
-                          : (const void*)k_exec_f32_32<WarpSmem32R>;
-  if (cls == CLS_F32_64)
-    return g_nwb64 == 8 ? (const void*)k_exec_f32_64<8>
-                        : (g_nwb64 == 2 ? (const void*)k_exec_f32_64<2>
-                                        : (g_nwb64 == 5 ? (const void*)k_exec_f32_64<4, 96>
-                                                        : (g_nwb64 == 6 ? (const void*)k_exec_f32_64<4, ROWS_PAIRED>
-                                                                        : (const void*)k_exec_f32_64<4>)));
-  return (const void*)k_exec_f64;
-}
+int exec_threads(int cls, const ExecCfg& c) { return variant(cls, c).threads; }
+size_t exec_smem(int cls, const ExecCfg& c) { return variant(cls, c).smem; }
+const void* exec_kernel_ptr(int cls, const ExecCfg& c) { return variant(cls, c).fn; }
 
 cudaError_t exec_setup(int device) {
   (void)device;
-  cudaError_t e = cudaFuncSetAttribute(k_exec_f32_32<WarpSmem32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM32);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_exec_f32_32<WarpSmem32P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM32P);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_exec_f32_32<WarpSmem32R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM32R);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_exec_f32_64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(CtaSmem64<4>));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_exec_f32_64<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(CtaSmem64<8>));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_exec_f32_64<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(CtaSmem64<2>));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_exec_f32_64<4, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(CtaSmem64<4, 96>));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_exec_f32_64<4, ROWS_PAIRED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(CtaSmem64<4, ROWS_PAIRED>));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_exec_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEMD);
+  for (const Variant& v : kVariants) {
+    const cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_init_out(const JobDev* jobs_dev, int n_jobs, int max_pixels, cudaStream_t st) {
@@ -2000,23 +2001,11 @@ cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st) {
+cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st, const ExecCfg& c) {
   if (grid <= 0) return cudaSuccess;
-  if (cls == CLS_F32_32 && g_lay32 == 1) k_exec_f32_32<WarpSmem32><<<grid, NW32 * 32, SMEM32, st>>>(a);
-  else if (cls == CLS_F32_32 && g_lay32 == 2) k_exec_f32_32<WarpSmem32P><<<grid, NW32 * 32, SMEM32P, st>>>(a);
-  else if (cls == CLS_F32_32) k_exec_f32_32<WarpSmem32R><<<grid, NW32 * 32, SMEM32R, st>>>(a);
-  else if (cls == CLS_F32_64 && g_nwb64 == 8)
-    k_exec_f32_64<8><<<grid, 256, sizeof(CtaSmem64<8>), st>>>(a);
-  else if (cls == CLS_F32_64 && g_nwb64 == 2)
-    k_exec_f32_64<2><<<grid, 64, sizeof(CtaSmem64<2>), st>>>(a);
-  else if (cls == CLS_F32_64 && g_nwb64 == 5)
-    k_exec_f32_64<4, 96><<<grid, 128, sizeof(CtaSmem64<4, 96>), st>>>(a);
-  else if (cls == CLS_F32_64 && g_nwb64 == 6)
-    k_exec_f32_64<4, ROWS_PAIRED><<<grid, 128, sizeof(CtaSmem64<4, ROWS_PAIRED>), st>>>(a);
-  else if (cls == CLS_F32_64)
-    k_exec_f32_64<4><<<grid, 128, sizeof(CtaSmem64<4>), st>>>(a);
-  else k_exec_f64<<<grid, NT64, SMEMD, st>>>(a);
-  return cudaGetLastError();
+  const Variant& v = variant(cls, c);
+  void* args[] = {const_cast<ExecArgs*>(&a)};
+  return cudaLaunchKernel(v.fn, dim3((unsigned)grid), dim3((unsigned)v.threads), args, v.smem, st);
 }
 
 cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st) {

@@ -28,6 +28,7 @@ constexpr int kMaxJobs = 16;
 constexpr int kMaxTiles = 1024;
 constexpr int kMaxDevices = 64;
 constexpr int kMaxWeights = kMaxJobs * 64 * 64;
+const ExecCfg kCfg;  // the default executor of every class (no context to tune)
 
 // The shared scratch.  In host code this name is only a stand-in for the
 // device array, never a device address: the address comes from
@@ -234,12 +235,10 @@ int run(const fse_job_t* jobs, int32_t n, cudaStream_t st) {
     if (cap[k] > 0) NOALLOC_CUDA(launch_deps(a, k, (int)cap[k], st));
   for (int k = 0; k < MAX_CLS; ++k)
     if (cap[k] > 0) {
-      // the executor layout of a class can change between calls (options,
-      // autotuner), so the persistent grid is sized for the current one
       int nb = 0;
-      NOALLOC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(k), exec_threads(k),
-                                                                 exec_smem(k)));
-      NOALLOC_CUDA(launch_exec(a, k, (nb > 0 ? nb : 1) * S.sm_count, st));
+      NOALLOC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, exec_kernel_ptr(k, kCfg),
+                                                                 exec_threads(k, kCfg), exec_smem(k, kCfg)));
+      NOALLOC_CUDA(launch_exec(a, k, (nb > 0 ? nb : 1) * S.sm_count, st, kCfg));
     }
   // the queue state comes back on the caller's stream: no device-wide sync
   NOALLOC_CUDA(cudaMemcpyAsync(g_q, base + o_q, sizeof(g_q), cudaMemcpyDeviceToHost, st));

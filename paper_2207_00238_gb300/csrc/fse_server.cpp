@@ -230,6 +230,11 @@ int fse_server_create(fse_server_t** out, fse_context_t* ctx, const fse_server_c
     ln.ctx->exec_mode = ctx->exec_mode;
     ln.ctx->ctas_per_sm = ctx->ctas_per_sm;
     ln.ctx->timeout_ms = ctx->timeout_ms;
+    ln.ctx->cfg = ctx->cfg;  // the parent context's executor variants and tuning
+    for (int k = 0; k < fse::MAX_CLS; ++k) ln.ctx->tuned_ctas[k] = ctx->tuned_ctas[k];
+    ln.ctx->concurrent = ctx->concurrent;
+    ln.ctx->class_order = ctx->class_order;
+    fse::update_occupancy(ln.ctx);
     ln.pinned_bytes = std::min<size_t>(s->lane_bytes / 2, (size_t)1 << 30);
     if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) != cudaSuccess ||
