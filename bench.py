@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="measured requests of the serving leg (0 = skip)")
     ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 6, 8])
-    ap.add_argument("--f32-layout", type=int, default=0, choices=[0, 1, 2, 3])
+    ap.add_argument("--f32-layout", type=int, default=0, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--no-tma", action="store_true", help="stage supports with plain loads")
     ap.add_argument("--no-graph", action="store_true", help="time direct launches instead of graph replay")
     ap.add_argument("--no-autotune", action="store_true")

@@ -167,8 +167,9 @@ void fse_context_destroy(fse_context_t* ctx);
                                    spectrum column per lane, 2 = bins paired
                                    for the two-wide FP32 instructions, 3 = one
                                    column per lane read in row runs (35-row W
-                                   table, 6 blocks of 2 warps per SM); 0 =
-                                   default (3)                                 */
+                                   table, 6 blocks of 2 warps per SM); 4 = the
+                                   same with plain-load staging only, 8 blocks
+                                   per SM; 0 = default (3)                     */
 #define FSE_OPT_TMA_STAGING 9   /* 1 = the F = 32 executor stages each block's
                                    support with TMA tensor copies where the
                                    job's image and mask are 16-byte aligned
@@ -186,7 +187,7 @@ void fse_context_destroy(fse_context_t* ctx);
                                    read with fse_context_class_times and
                                    fse_context_kernel_times                   */
 #define FSE_OPT_F32_UNROLL 11   /* K-loop unroll factor of the F = 32 executor:
-                                   1 (default) or 2 (layouts 2 and 3)          */
+                                   1 (default) or 2 (layouts 2, 3 and 4)       */
 #define FSE_OPT_F64_UNROLL 12   /* K-loop unroll factor of the F = 64 executor:
                                    1 (default) or 2 (layout 6)                 */
 #define FSE_OPT_CLASS_LAUNCH 13 /* work classes of one call (F = 32, F = 64,
@@ -223,7 +224,7 @@ int32_t fse_context_class_times(fse_context_t* ctx, float* ms, int32_t cap);
  * fse_autotune -- times the given job mix (device pointers, as for
  * fse_extrapolate_batch; the outputs are written) under candidate launch
  * configurations of each work class present: the executor layout
- * (FSE_OPT_F64_WARPS 6, 4, 5, 2, 8; FSE_OPT_F32_LAYOUT 3, 2, 1), the K-loop
+ * (FSE_OPT_F64_WARPS 6, 4, 5, 2, 8; FSE_OPT_F32_LAYOUT 3, 4, 2, 1), the K-loop
  * unroll factor (1, 2 where the layout has it) and the persistent CTAs per
  * SM; then, for a mix of classes, the class launch (FSE_OPT_CLASS_LAUNCH 0, 1,
  * 2).  Each candidate runs `reps` times (median of the iteration-kernel time);

@@ -108,11 +108,11 @@ int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int 
   c->concurrent = 0;
   struct Cand { int lay, un, ctas_span; };
   const Cand cand64[] = {{6, 1, 1}, {6, 2, 1}, {4, 1, 1}, {5, 1, 1}, {2, 1, 1}, {8, 1, 1}};
-  const Cand cand32[] = {{3, 1, 3}, {3, 2, 3}, {2, 1, 3}, {2, 2, 3}, {1, 1, 3}};
+  const Cand cand32[] = {{3, 1, 3}, {3, 2, 3}, {4, 1, 3}, {4, 2, 3}, {2, 1, 3}, {2, 2, 3}, {1, 1, 3}};
   for (int cls : {CLS_F32_64, CLS_F32_32}) {
     if (!present[cls] || rc != FSE_OK) continue;
     const Cand* cands = cls == CLS_F32_64 ? cand64 : cand32;
-    const int ncand = cls == CLS_F32_64 ? 6 : 5;
+    const int ncand = cls == CLS_F32_64 ? 6 : 7;
     int& lay = cls == CLS_F32_64 ? c->cfg.lay64 : c->cfg.lay32;
     int& un = cls == CLS_F32_64 ? c->cfg.unroll64 : c->cfg.unroll32;
     double best = 1e30;
@@ -287,7 +287,7 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       return FSE_OK;
     case FSE_OPT_F32_LAYOUT: {
       const int lay = value == 0 ? 3 : (int)value;
-      if (value < 0 || value > 3) return fse::fail(FSE_EINVAL, "f32 layout");
+      if (value < 0 || value > 4) return fse::fail(FSE_EINVAL, "f32 layout");
       c->cfg.lay32 = lay;
       if (!fse::exec_cfg_valid(fse::CLS_F32_32, lay, c->cfg.unroll32)) c->cfg.unroll32 = 1;
       fse::update_occupancy(c);

@@ -104,9 +104,10 @@ struct ExecArgs {
 
 // Executor configuration of one context: which kernel variant runs each work
 // class.  F = 32 layouts: 1 one spectrum column per lane, 2 paired bins, 3 row
-// runs; F = 64 layouts: 2, 4, 8 warps per block, 5 four warps with a 96-row
-// table, 6 four warps with paired bins.  unroll: K-loop unroll factor (1 or 2;
-// 2 exists for layouts 2, 3 and 6).
+// runs, 4 row runs with plain-load staging only (8 CTAs per SM); F = 64
+// layouts: 2, 4, 8 warps per block, 5 four warps with a 96-row table, 6 four
+// warps with paired bins.  unroll: K-loop unroll factor (1 or 2; 2 exists for
+// F = 32 layouts 2, 3, 4 and F = 64 layout 6).
 struct ExecCfg {
   int32_t lay32 = 3;
   int32_t lay64 = 6;

@@ -1062,25 +1062,34 @@ constexpr size_t SMEM32P = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32P);
 // warp) and the table overlays the FFT buffer.  Same arithmetic and keys as
 // the column layout; more warps fit on an SM.
 // ---------------------------------------------------------------------------
-struct alignas(128) WarpSmem32R {
+// PAD = 3712: bytes 8192..15871 from Wd take the TMA support boxes.  The
+// compact form (PAD = 16, layout 4) stages with plain loads only and fits
+// 8 CTAs of 2 warps per SM at 128 registers per thread.
+template <int PAD>
+struct alignas(128) WarpSmem32RT {
   float2 Wd[35 * 32];  // W rows 0..31, rows 32..34 repeat rows 0..2; rows 0..31 double as FFT buffer
   float2 coef_d[KMAX];
   int32_t coef_u[KMAX];
   float red[32];
-  unsigned char stage_pad[3712];  // bytes 8192..15871 from Wd take the TMA support boxes
+  unsigned char stage_pad[PAD];
   uint64_t mbar;
   uint32_t tma_ph;
   TileDev T;
   JobDev J;
 };
+using WarpSmem32R = WarpSmem32RT<3712>;
+using WarpSmem32C = WarpSmem32RT<16>;
 
-template <int U>
-__device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WarpSmem32R& sm, const float2* tw,
+template <int U, class WS>
+__device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, const float2* tw,
                                              int lane) {
   const ClassArgs& C = a.c[CLS_F32_32];
   float2 x[32];
   float rbar;
-  if (!stage_fft32(a, id, sm, sm.Wd, lane, x, reinterpret_cast<unsigned char*>(sm.Wd) + 8192, 7680, rbar)) return false;
+  constexpr bool kTma = std::is_same<WS, WarpSmem32R>::value;  // the compact form has no box space
+  if (!stage_fft32(a, id, sm, sm.Wd, lane, x, kTma ? reinterpret_cast<unsigned char*>(sm.Wd) + 8192 : nullptr,
+                   kTma ? 7680 : 0, rbar))
+    return false;
   const int2 it = C.items[id];
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -1174,16 +1183,20 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WarpSmem
   return true;
 }
 constexpr size_t SMEM32R = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32R);
+constexpr size_t SMEM32C = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32C);
 
 template <class WS, int U>
 __device__ __forceinline__ bool run_item32(const ExecArgs& a, int id, WS& sm, const float2* tw, int lane) {
   if constexpr (std::is_same<WS, WarpSmem32P>::value) return item_f32_32p<U>(a, id, sm, tw, lane);
-  else if constexpr (std::is_same<WS, WarpSmem32R>::value) return item_f32_32r<U>(a, id, sm, tw, lane);
+  else if constexpr (std::is_same<WS, WarpSmem32R>::value || std::is_same<WS, WarpSmem32C>::value)
+    return item_f32_32r<U>(a, id, sm, tw, lane);
   else return item_f32_32(a, id, sm, tw, lane);
 }
 
 template <class WS, int U>
-__global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32R>::value ? 6 : 5)
+__global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32C>::value
+                                                 ? 8
+                                                 : (std::is_same<WS, WarpSmem32R>::value ? 6 : 5))
     k_exec_f32_32(const __grid_constant__ ExecArgs a) {
   extern __shared__ __align__(128) unsigned char smem32_raw[];
   float2* tw = reinterpret_cast<float2*>(smem32_raw);
@@ -1939,6 +1952,8 @@ const Variant kVariants[] = {
     {CLS_F32_32, 2, 1, (const void*)k_exec_f32_32<WarpSmem32P, 1>, NW32 * 32, SMEM32P},
     {CLS_F32_32, 2, 2, (const void*)k_exec_f32_32<WarpSmem32P, 2>, NW32 * 32, SMEM32P},
     {CLS_F32_32, 1, 1, (const void*)k_exec_f32_32<WarpSmem32, 1>, NW32 * 32, SMEM32},
+    {CLS_F32_32, 4, 1, (const void*)k_exec_f32_32<WarpSmem32C, 1>, NW32 * 32, SMEM32C},
+    {CLS_F32_32, 4, 2, (const void*)k_exec_f32_32<WarpSmem32C, 2>, NW32 * 32, SMEM32C},
     {CLS_F32_64, 6, 1, (const void*)k_exec_f32_64<4, ROWS_PAIRED, 1>, 128, sizeof(CtaSmem64<4, ROWS_PAIRED>)},
     {CLS_F32_64, 6, 2, (const void*)k_exec_f32_64<4, ROWS_PAIRED, 2>, 128, sizeof(CtaSmem64<4, ROWS_PAIRED>)},
     {CLS_F32_64, 5, 1, (const void*)k_exec_f32_64<4, 96>, 128, sizeof(CtaSmem64<4, 96>)},

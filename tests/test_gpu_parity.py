@@ -87,7 +87,7 @@ def _seq_check(oracle_lib, ctx, job, **over):
     assert (got[0]["out"] == ref["out"]).all()
 
 
-@pytest.mark.parametrize("layout", [1, 2, 3])
+@pytest.mark.parametrize("layout", [1, 2, 3, 4])
 @pytest.mark.parametrize("case", ["plain_64", "defects_small"])
 def test_fp32_f32_executor_layouts(ctx, oracle_lib, layout, case):
     """Each layout of the F = 32 executor meets the FP32 gate."""
@@ -144,19 +144,21 @@ def test_tma_staging_small_support(ctx, oracle_lib, layout32):
 
 
 def test_f32_run_layout_matches_column_layout(ctx):
-    """The row-run layout of the F = 32 executor does the column layout's
-    arithmetic in the same order: identical bytes and model values."""
+    """The row-run layouts of the F = 32 executor (TMA-capable and compact) do
+    the column layout's arithmetic in the same order: identical bytes and model
+    values."""
     jobs = [CASES["plain_64"](), CASES["defects_small"]()]
     res = {}
-    for layout in (1, 3):
+    for layout in (1, 3, 4):
         ctx.set_option(fse.OPT_F32_LAYOUT, layout)
         try:
             res[layout], _ = run_gpu(ctx, jobs)
         finally:
             ctx.set_option(fse.OPT_F32_LAYOUT, 0)
-    for a, b in zip(res[1], res[3]):
-        assert (a["out"] == b["out"]).all()
-        np.testing.assert_array_equal(a["g"], b["g"])
+    for other in (3, 4):
+        for a, b in zip(res[1], res[other]):
+            assert (a["out"] == b["out"]).all()
+            np.testing.assert_array_equal(a["g"], b["g"])
 
 
 @pytest.mark.parametrize("warps", [2, 4, 5, 6, 8])
