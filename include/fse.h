@@ -190,6 +190,11 @@ void fse_context_destroy(fse_context_t* ctx);
                                    1 (default) or 2 (layouts 2, 3 and 4)       */
 #define FSE_OPT_F64_UNROLL 12   /* K-loop unroll factor of the F = 64 executor:
                                    1 (default) or 2 (layout 6)                 */
+#define FSE_OPT_SERVER_CLASSES 14 /* work classes the resident executor of a
+                                   server made from this context runs: 1 = FP32
+                                   F = 32, 2 = FP32 F = 64, 3 (default) = both
+                                   (the F = 64 executor one CTA per SM below its
+                                   occupancy, the compact F = 32 layout beside) */
 #define FSE_OPT_CLASS_LAUNCH 13 /* work classes of one call (F = 32, F = 64,
                                    FP64): 0 = launched one after the other;
                                    1 (default) = concurrently on forked streams,
@@ -291,11 +296,13 @@ int fse_extrapolate_noalloc(const fse_job_t* jobs, int32_t n, void* cuda_stream)
 /* ---- serving: continuous batching ---------------------------------------- */
 typedef struct fse_server fse_server_t;
 typedef struct fse_server_cfg_t {
-    size_t arena_bytes;    /* device bytes for resident request state; cut into
-                              4 lanes, each running one batch at a time       */
+    size_t arena_bytes;    /* device bytes for the server: its work queues (a
+                              quarter at most) and the resident requests'
+                              buffers                                          */
     int32_t max_queue;     /* pending requests before FSE_EBUSY (0 = 64)     */
-    int32_t max_resident;  /* requests resident on the GPU at once (0 = 64)  */
-    int32_t max_batch;     /* requests per lane launch (0 = 16)              */
+    int32_t max_resident;  /* requests resident on the GPU at once (0 = 64,
+                              at most 256)                                     */
+    int32_t max_batch;     /* unused (kept for the layout of this struct)    */
 } fse_server_cfg_t;
 
 #define FSE_REQ_QUEUED 0
@@ -304,25 +311,39 @@ typedef struct fse_server_cfg_t {
 #define FSE_REQ_FAILED 3
 
 /*
- * fse_server_create -- starts the serving thread on the context's GPU (the
- * context supplies the device and its options; its arena is not used).  The
- * server reserves cfg->arena_bytes of device memory (FSE_ENOMEM if that much
- * is not free) in 4 lanes.  Continuous batching: whenever a lane is free, the
- * queued requests that fit its device bytes (an upper-bound estimate per
- * request) are admitted in arrival order and launched as one batch on the
- * lane's stream; lanes run concurrently, so requests arriving while others are
- * on the GPU start as soon as a lane frees up.  Every result equals the result
- * of the same job run alone.  fse_server_destroy finishes queued and running
- * requests first.
+ * fse_server_create -- starts a continuous-batching server on the context's
+ * GPU (the context supplies the device, the executor layouts and options,
+ * FSE_OPT_SERVER_CLASSES; its arena is not used).  The server reserves
+ * cfg->arena_bytes of device memory (FSE_ENOMEM if that much is not free) and
+ * launches one resident persistent executor per served class, which runs
+ * until the server is destroyed and drains one work queue per class shared by
+ * all resident requests.  A worker thread admits queued requests in arrival
+ * order whenever a resident slot and device memory are free: it copies the
+ * request in and posts it to the running executor, whose next idle group
+ * enumerates the request's lost blocks and queues the ready ones, so a new
+ * request's blocks run beside those of the requests already on the GPU (no
+ * launch per request or batch).  Every wait of the executor is bounded by a
+ * heartbeat of the worker and by FSE_OPT_TIMEOUT_MS.  Every result equals the
+ * result of the same job run alone.  Serves FP32 jobs; fse_server_destroy
+ * finishes queued and running requests first.
  */
 int fse_server_create(fse_server_t** srv, fse_context_t* ctx, const fse_server_cfg_t* cfg);
 /*
  * fse_submit -- queues one job; image/mask/out/out_f32 are HOST pointers.
  * image and mask are copied before the call returns; out (and out_f32) must
- * stay valid until fse_wait returns for this ticket.  FSE_EBUSY when full.
+ * stay valid until fse_wait returns for this ticket.  FSE_EBUSY when the queue
+ * is full; FSE_EINVAL for an FP64 job, a class the server does not run, or
+ * more than 64 tiles; FSE_ENOMEM when the job can never fit the server.
  */
 int fse_submit(fse_server_t* srv, const fse_job_t* job, uint64_t* ticket);
 int fse_poll(fse_server_t* srv, uint64_t ticket, int32_t* state);
+/*
+ * fse_cancel -- cancels a request: a queued one leaves the queue, a running
+ * one has its remaining blocks skipped (they are only released, so other
+ * requests are unaffected).  Either way fse_wait then returns FSE_ECANCELLED;
+ * a request already done is not changed.  FSE_ENOTFOUND for an unknown ticket.
+ */
+int fse_cancel(fse_server_t* srv, uint64_t ticket);
 /* Waits up to timeout_ms (< 0: no limit) for completion; st may be NULL.
  * Returns FSE_OK, the request's error status, FSE_ETIMEOUT or FSE_ENOTFOUND.
  * A completed ticket is forgotten after fse_wait returns FSE_OK for it. */
@@ -344,6 +365,18 @@ const char* fse_last_error(void);
  */
 int32_t fse_debug_fetch(fse_context_t* ctx, int32_t* rec, int32_t* useq, int32_t cap,
                         int32_t* K_max);
+
+/*
+ * fse_server_debug_state -- a snapshot of a server's state for diagnosis:
+ * per FP32 class (F = 32, then F = 64) 8 values: items enumerated, queue
+ * positions reserved, positions filled, blocks done, admit commands posted and
+ * taken (device), commands posted and queue entries reserved (host); then per
+ * job slot (256) 8 values: ticket (-1 free), generation (host), generation,
+ * lost blocks and blocks done (device), completed generation (host-mapped),
+ * cancelled generation (device), request state.  out holds cap >= 2064
+ * values.  Returns the count written.
+ */
+int32_t fse_server_debug_state(fse_server_t* srv, int64_t* out, int32_t cap);
 
 /*
  * fse_debug_wait_probe -- launches the work-queue consumer on an empty queue

@@ -21,7 +21,7 @@ ORDER = {"phased": 0, "raster": 1, "independent": 2}
 TILING = {"alg1": 0, "vertical": 1}
 OPT_EXEC_MODE, OPT_TIMEOUT_MS, OPT_CTAS_PER_SM, OPT_USE_GRAPH, OPT_DEBUG_CAPTURE, OPT_KERNEL_TIMING = 1, 2, 3, 4, 5, 6
 OPT_F64_WARPS, OPT_F32_LAYOUT, OPT_TMA_STAGING, OPT_DEBUG_TMA_STALL = 7, 8, 9, 10
-OPT_F32_UNROLL, OPT_F64_UNROLL, OPT_CLASS_LAUNCH = 11, 12, 13
+OPT_F32_UNROLL, OPT_F64_UNROLL, OPT_CLASS_LAUNCH, OPT_SERVER_CLASSES = 11, 12, 13, 14
 EXEC = {"dag": 0, "levels": 1, "per_block": 2}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
@@ -75,7 +75,7 @@ EXPORTS = ["fse_plan_tiles", "fse_plan_tiles_vertical", "fse_context_create", "f
            "fse_extrapolate_batch", "fse_extrapolate_host", "fse_server_create", "fse_submit",
            "fse_poll", "fse_wait", "fse_server_latencies", "fse_server_destroy", "fse_last_error",
            "fse_debug_fetch", "fse_debug_wait_probe", "fse_context_kernel_times",
-           "fse_extrapolate_noalloc", "fse_autotune", "fse_context_class_times"]
+           "fse_extrapolate_noalloc", "fse_autotune", "fse_context_class_times", "fse_cancel", "fse_server_debug_state"]
 
 _lib = None
 
@@ -100,6 +100,9 @@ def load(path=LIB_PATH):
     L.fse_server_create.argtypes = [P(vp), vp, P(ServerCfg)]
     L.fse_submit.argtypes = [vp, P(Job), P(ctypes.c_uint64)]
     L.fse_poll.argtypes = [vp, ctypes.c_uint64, P(i32)]
+    L.fse_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.fse_server_debug_state.argtypes = [vp, P(ctypes.c_int64), i32]
+    L.fse_server_debug_state.restype = i32
     L.fse_wait.argtypes = [vp, ctypes.c_uint64, i32, P(Stats)]
     L.fse_server_latencies.argtypes = [vp, P(ctypes.c_double), i32]
     L.fse_server_latencies.restype = i32
@@ -275,6 +278,9 @@ class Server:
         self._keep[t.value] = (out, out_f32)
         return t.value
 
+    def cancel(self, ticket):
+        _check(load().fse_cancel(self.h, ticket))
+
     def poll(self, ticket):
         st = ctypes.c_int32(0)
         _check(load().fse_poll(self.h, ticket, ctypes.byref(st)))
@@ -287,6 +293,14 @@ class Server:
             self._keep.pop(ticket, None)
         _check(rc)
         return st.as_dict()
+
+    def debug_state(self):
+        """fse_server_debug_state: per class and per occupied slot counters."""
+        buf = (ctypes.c_int64 * 2064)()
+        n = _check(load().fse_server_debug_state(self.h, buf, 2064))
+        a = list(buf[:n])
+        slots = [a[16 + 8 * i:24 + 8 * i] for i in range(256)]
+        return {"f32": a[0:8], "f64": a[8:16], "slots": [s for s in slots if s[0] != -1]}
 
     def latencies(self, cap=1 << 20):
         buf = (ctypes.c_double * cap)()

@@ -311,6 +311,10 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       fse::update_occupancy(c);
       return FSE_OK;
     }
+    case FSE_OPT_SERVER_CLASSES:
+      if (value < 1 || value > 3) return fse::fail(FSE_EINVAL, "server classes %d", (int)value);
+      c->server_classes = (int)value;
+      return FSE_OK;
     case FSE_OPT_CLASS_LAUNCH:
       if (value < 0 || value > 2) return fse::fail(FSE_EINVAL, "class launch %d", (int)value);
       c->concurrent = value != 0;

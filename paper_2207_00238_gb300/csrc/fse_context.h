@@ -30,6 +30,7 @@ struct fse_context {
   int tma = 2;  // TMA staging of F = 32 supports: 0 off, 1 where the buffers allow it, 2 auto
   int capturing = 0;
   int dbg_tma_stall = 0;  // test only (FSE_OPT_DEBUG_TMA_STALL)
+  int server_classes = 3;  // FSE_OPT_SERVER_CLASSES of servers made from this context
   std::vector<cudaEvent_t> tev;  // pairs: start, end of the iteration kernels
   size_t tev_used = 0;
   fse::ExecCfg cfg;                    // executor variant per class (options, autotuner)

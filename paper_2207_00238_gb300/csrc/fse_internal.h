@@ -81,6 +81,43 @@ struct ClassArgs {
   int32_t cap;
 };
 
+// Continuous-batching server state (fse_server.cpp).  Work items of every
+// resident request share one queue per class that lives as long as the
+// server; a request joins by an "admit" command that the resident executor
+// itself carries out (output init, lost-block enumeration, dependency counts,
+// first pushes), so no other kernel needs SM resources while it runs.
+constexpr int SRV_MAXJ = 256;      // job slots (resident requests)
+constexpr int SRV_MAXT = 64;       // tiles per request
+constexpr int SRV_CMD_RING = 1024; // posted, not yet taken admit commands per class
+constexpr int32_t SRV_CMD_BIT = 0x40000000;  // queue entry = command index | SRV_CMD_BIT
+
+struct ServerCmd {
+  int32_t job, gen, n_tiles, pad_;
+};
+
+// Device-memory control block.  The host writes its fields with small
+// stream-ordered copies (a record before the count that publishes it); the
+// resident executor reads them with acquire loads.
+struct ServerDevCtl {
+  int32_t stop;       // host: 1 = exit once idle
+  int32_t heartbeat;  // host: advanced by the server's worker; stale => host gone
+  int32_t cmd_tail[MAX_CLS];  // host: admit commands posted per class
+  int32_t cmd_taken[MAX_CLS]; // device: commands moved into the work queue
+  int32_t pad_[3];
+  ServerCmd cmd[MAX_CLS][SRV_CMD_RING];  // host
+  int32_t cancel_gen[SRV_MAXJ];  // host: the slot's job of this generation is cancelled
+  int32_t total[SRV_MAXJ];       // device: lost blocks of the slot's job (its admit)
+  int32_t done[SRV_MAXJ];        // device: blocks of the slot's job finished
+  int32_t gen[SRV_MAXJ];         // device: generation of the slot's current job
+};
+
+// Host-mapped block written by the device.
+struct ServerHostCtl {
+  int32_t done_gen[SRV_MAXJ];  // generation of the last job completed in the slot
+  int32_t error;               // ErrBits
+  int32_t pad_[3];
+};
+
 struct ExecArgs {
   const JobDev* jobs;
   const TileDev* tiles;
@@ -98,6 +135,10 @@ struct ExecArgs {
   int32_t level;
   int32_t single_item;  // >= 0: process exactly this item (per-block launch)
   int32_t dbg_tma_stall;  // test only: TMA stagings never complete their mbarrier phase
+  // server mode (0 = one batch call): the resident executor of fse_server
+  int32_t server;
+  ServerDevCtl* srv;
+  ServerHostCtl* host;  // device address of the host-mapped control block
   int32_t* level_of;    // per class item level (levels mode), class stride level_stride
   int64_t level_stride;
 };

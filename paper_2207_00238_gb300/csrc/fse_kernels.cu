@@ -62,6 +62,28 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Reads of data that may be written while the kernel runs (the server's
+// descriptors, items, block maps and request buffers, written by the host's
+// copies or by other SMs) go to L2 (ld.global.cg): L1 and the read-only path
+// are not coherent across SMs, and a resident server kernel outlives those
+// writes.
+template <typename T_>
+__device__ __forceinline__ T_ ldcg_struct(const T_* p) {
+  static_assert(sizeof(T_) % 4 == 0, "descriptor size");
+  T_ v;
+  int* d = reinterpret_cast<int*>(&v);
+  const int* q = reinterpret_cast<const int*>(p);
+#pragma unroll 4
+  for (int i = 0; i < (int)(sizeof(T_) / 4); ++i) d[i] = __ldcg(q + i);
+  return v;
+}
+
+// Barrier of a block's thread group: the CTA, or one warp.
+template <bool CTA>
+__device__ __forceinline__ void bar() {
+  if constexpr (CTA) __syncthreads(); else __syncwarp();
+}
+
 // Processing-order key (PHASED: phase, I, J; RASTER: I, J).
 __device__ __forceinline__ int64_t order_key(const JobDev& J, int I, int Jb) {
   int64_t k = ((int64_t)I << 20) | (int64_t)Jb;
@@ -112,6 +134,24 @@ __device__ int queue_pop_warp(const ClassArgs& C, int64_t timeout_ns, int lane) 
   return __shfl_sync(0xffffffffu, item, 0);
 }
 
+// Lost predecessors of block (I, Jb) inside its dependency window: under
+// PHASED the window's lost blocks of lower phase, under RASTER the earlier
+// ones, under INDEPENDENT none.
+__device__ __forceinline__ int count_preds(const JobDev& J, const TileDev& T, const int32_t* map, int I, int Jb) {
+  if (J.order == ORDER_INDEPENDENT) return 0;
+  const int D = J.D;
+  const int64_t kx = order_key(J, I, Jb);
+  int cnt = 0;
+  for (int dI = -D; dI <= D; ++dI)
+    for (int dJ = -D; dJ <= D; ++dJ) {
+      const int I2 = I + dI, J2 = Jb + dJ;
+      if (I2 < 0 || I2 >= T.nby || J2 < 0 || J2 >= T.nbx) continue;
+      const int id2 = __ldcg(map + I2 * T.nbx + J2);
+      if (id2 >= 0 && order_key(J, I2, J2) < kx) ++cnt;
+    }
+  return cnt;
+}
+
 // After a block's writes are globally visible: decrement the pending count
 // of every later lost block in its dependency window, queue those reaching 0.
 __device__ __forceinline__ void release_successors(const ExecArgs& a, const ClassArgs& C, const TileDev& T,
@@ -123,13 +163,194 @@ __device__ __forceinline__ void release_successors(const ExecArgs& a, const Clas
   for (int pos = t; pos < wd * wd; pos += nthr) {
     const int I2 = I + pos / wd - D, J2 = Jb + pos % wd - D;
     if (I2 < 0 || I2 >= T.nby || J2 < 0 || J2 >= T.nbx) continue;
-    const int id2 = map[I2 * T.nbx + J2];
+    const int id2 = __ldcg(map + I2 * T.nbx + J2);
     if (id2 < 0 || order_key(J, I2, J2) <= kx) continue;
     if (atomicSub(&C.cnt[id2], 1) == 1) {
       __threadfence();
       queue_push(C, id2);
     }
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Server mode: the resident executor of the continuous-batching server.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void st_release_sys(int* p, int v) {
+  asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Moves one posted admit command of class cls into the work queue (any
+// consumer may do it; a CAS on the taken count gives each command to one).
+__device__ __forceinline__ void server_take_command(const ExecArgs& a, const ClassArgs& C, int cls) {
+  ServerDevCtl* d = a.srv;
+  const int tail = ld_acquire(&d->cmd_tail[cls]);
+  int taken = ld_relaxed(&d->cmd_taken[cls]);
+  while (taken < tail) {
+    const int got = atomicCAS(&d->cmd_taken[cls], taken, taken + 1);
+    if (got == taken) {
+      queue_push(C, SRV_CMD_BIT | taken);
+      return;
+    }
+    taken = got;
+  }
+}
+
+// Server pop (lane 0's result broadcast to the warp): reserves the next queue
+// slot and waits for its entry, taking posted commands into the queue while
+// it waits.  Returns an item id, a command (SRV_CMD_BIT | index), -1 when the
+// server stops, -2 when the host's heartbeat has been stale for timeout_ns
+// (the host is gone) or the queue's capacity ran out.
+__device__ int server_pop_warp(const ExecArgs& a, const ClassArgs& C, int cls, int lane) {
+  int item = -1;
+  if (lane == 0) {
+    ServerDevCtl* d = a.srv;
+    if (ld_acquire(&d->stop)) {
+      item = -1;
+    } else {
+      const int pos = atomicAdd(&C.q->head, 1);
+      if (pos >= C.cap) {
+        atomicOr(&a.host->error, ERR_BOUNDS);
+        item = -2;
+      } else {
+        int hb = ld_relaxed(&d->heartbeat);
+        uint64_t t_hb = global_ns();
+        unsigned sleep_ns = 32;
+        for (;;) {
+          item = ld_acquire(&C.slots[pos]);
+          if (item != -1) break;
+          server_take_command(a, C, cls);
+          if (ld_acquire(&d->stop)) {
+            item = -1;
+            break;
+          }
+          const int h = ld_relaxed(&d->heartbeat);
+          const uint64_t now = global_ns();
+          if (h != hb) {
+            hb = h;
+            t_hb = now;
+          } else if ((int64_t)(now - t_hb) > a.timeout_ns) {
+            atomicOr(&a.host->error, ERR_TIMEOUT);
+            item = -2;
+            break;
+          }
+          __nanosleep(sleep_ns);
+          if (sleep_ns < 4096) sleep_ns <<= 1;
+        }
+      }
+    }
+  }
+  return __shfl_sync(0xffffffffu, item, 0);
+}
+
+// One block of a job finished (or was skipped): the job completes with its
+// last block, which publishes the job's generation to the host.
+__device__ __forceinline__ void server_block_done(const ExecArgs& a, int job) {
+  ServerDevCtl* d = a.srv;
+  const int n = atomicAdd(&d->done[job], 1) + 1;
+  if (n == ld_relaxed(&d->total[job])) {
+    __threadfence_system();
+    st_release_sys(&a.host->done_gen[job], ld_relaxed(&d->gen[job]));
+  }
+}
+
+// Whether the item's job has been cancelled (its generation marked).
+__device__ __forceinline__ bool server_cancelled(const ExecArgs& a, const ClassArgs& C, int id) {
+  const int job = __ldcg(&a.tiles[__ldcg(C.items + id).x].job);
+  return ld_relaxed(&a.srv->cancel_gen[job]) == ld_relaxed(&a.srv->gen[job]);
+}
+
+// Admit command: makes job `j` (its descriptors, tiles and buffers written by
+// the host) resident in the running executor.  The group's t of nthr threads
+// write its known pixels to the output, mark its value planes pending,
+// enumerate its lost blocks into the
+// class's items, set every item's pending-predecessor count, and only then
+// push the items without predecessors (so no block of the job runs before all
+// counts are set).  The pushes recount instead of reading cnt, which running
+// blocks already decrement.
+template <bool CTA>
+__device__ void server_admit(const ExecArgs& a, const ClassArgs& C, int cls, int cmd, int t, int nthr) {
+  const ServerCmd rc = ldcg_struct(&a.srv->cmd[cls][cmd % SRV_CMD_RING]);
+  const int j = rc.job, gen = rc.gen, nt = rc.n_tiles;
+  const JobDev J = ldcg_struct(a.jobs + j);
+  ServerDevCtl* d = a.srv;
+  if (t == 0) {
+    d->done[j] = 0;
+    d->total[j] = 0;
+    d->gen[j] = gen;
+  }
+  const int64_t npx = (int64_t)J.W * J.H;
+  for (int64_t p = t; p < npx; p += nthr) {
+    const int y = (int)(p / J.W), x = (int)(p - (int64_t)y * J.W);
+    const size_t gi = (size_t)y * J.pitch + x;
+    const uint8_t v = __ldcg(J.mask + gi) ? 0 : __ldcg(J.image + gi);
+    J.out[gi] = v;
+    if (J.out_f32) J.out_f32[p] = (float)v;
+  }
+  for (int ti = 0; ti < nt; ++ti) {  // value planes: every pixel pending (NaN)
+    const TileDev T = ldcg_struct(a.tiles + j * SRV_MAXT + ti);
+    float* plane = a.val_f + T.val_off;
+    const int64_t n = (int64_t)T.ew * T.eh;
+    for (int64_t p = t; p < n; p += nthr) plane[p] = __int_as_float(-1);
+  }
+  bar<CTA>();
+  int local = 0;
+  for (int ti = 0; ti < nt; ++ti) {
+    const int tile = j * SRV_MAXT + ti;
+    const TileDev T = ldcg_struct(a.tiles + tile);
+    const int nb = T.nbx * T.nby;
+    for (int k = t; k < nb; k += nthr) {
+      const int I = k / T.nbx, Jb = k - I * T.nbx;
+      bool lost = false;
+      const int y0 = I * J.b, x0 = Jb * J.b;
+      for (int yy = y0; yy < min(y0 + J.b, T.eh) && !lost; ++yy)
+        for (int xx = x0; xx < min(x0 + J.b, T.ew); ++xx)
+          if (__ldcg(J.mask + (size_t)(T.ey + yy) * J.pitch + T.ex + xx)) {
+            lost = true;
+            break;
+          }
+      int id = -1;
+      if (lost) {
+        id = atomicAdd(&C.q->n_items, 1);
+        if (id < C.cap) {
+          C.items[id] = make_int2(tile, (I << 16) | Jb);
+          ++local;
+        } else {
+          atomicOr(&a.host->error, ERR_BOUNDS);
+          id = -1;
+        }
+      }
+      a.map[T.map_off + k] = id;
+    }
+  }
+  if (local) atomicAdd(&d->total[j], local);
+  __threadfence();
+  bar<CTA>();
+  for (int ti = 0; ti < nt; ++ti) {
+    const TileDev T = ldcg_struct(a.tiles + j * SRV_MAXT + ti);
+    const int32_t* map = a.map + T.map_off;
+    const int nb = T.nbx * T.nby;
+    for (int k = t; k < nb; k += nthr) {
+      const int id = __ldcg(map + k);
+      if (id >= 0) C.cnt[id] = count_preds(J, T, map, k / T.nbx, k % T.nbx);
+    }
+  }
+  __threadfence();
+  bar<CTA>();
+  if (t == 0 && ld_relaxed(&d->total[j]) == 0) {  // nothing lost: done at once
+    __threadfence_system();
+    st_release_sys(&a.host->done_gen[j], gen);
+  }
+  for (int ti = 0; ti < nt; ++ti) {
+    const TileDev T = ldcg_struct(a.tiles + j * SRV_MAXT + ti);
+    const int32_t* map = a.map + T.map_off;
+    const int nb = T.nbx * T.nby;
+    for (int k = t; k < nb; k += nthr) {
+      const int id = __ldcg(map + k);
+      if (id >= 0 && count_preds(J, T, map, k / T.nbx, k % T.nbx) == 0) queue_push(C, id);
+    }
+  }
+  bar<CTA>();
 }
 
 __device__ __forceinline__ uint8_t to_u8(float g) {
@@ -189,9 +410,9 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
       in[u] = col_in && m < S && ty >= 0 && ty < eh;
       const size_t gi = in[u] ? g0 + (size_t)ty * pitch + tx : g0;
       const size_t vi = in[u] ? (size_t)ty * vp + tx : 0;
-      wi[u] = __ldg(wiso + (m < S ? m * S + n : n));
-      mk[u] = __ldg(mask + gi);
-      px[u] = __ldg(image + gi);
+      wi[u] = __ldcg(wiso + (m < S ? m * S + n : n));
+      mk[u] = __ldcg(mask + gi);
+      px[u] = __ldcg(image + gi);
       v[u] = __ldcg(val + vi);
     }
 #pragma unroll
@@ -330,7 +551,7 @@ __device__ __forceinline__ void stage_from_boxes(const TileDev& T, const JobDev&
     const int ty = oy + m;
     float wv = 0.f, rv = 0.f;
     if (col_in && ty >= 0 && ty < T.eh) {
-      const float wi = __ldg(wiso + m * S + n);
+      const float wi = __ldcg(wiso + m * S + n);
       const int mk = smask[m * bw + dx8 + n];
       if (mk == 0) {
         wv = wi;
@@ -467,7 +688,7 @@ __device__ __forceinline__ void copy_desc(T_* dst, const T_* src, int t, int nth
   static_assert(sizeof(T_) % 4 == 0, "descriptor size");
   const int* s = reinterpret_cast<const int*>(src);
   int* d = reinterpret_cast<int*>(dst);
-  for (int i = t; i < (int)(sizeof(T_) / 4); i += nthr) d[i] = __ldg(s + i);
+  for (int i = t; i < (int)(sizeof(T_) / 4); i += nthr) d[i] = __ldcg(s + i);
 }
 
 // Second radix-2 step of a 64-point transform split over lanes l and l ^ 16:
@@ -487,10 +708,6 @@ __device__ __forceinline__ void fft64_combine(float2 (&x)[32], int h) {
   }
 }
 
-template <bool CTA>
-__device__ __forceinline__ void bar() {
-  if constexpr (CTA) __syncthreads(); else __syncwarp();
-}
 
 // Model evaluation at the block's b x b pixels and write-back (all executors).
 // coef_u / coef_d hold the K selected (u, Delta) pairs; tw[q] = exp(+2 pi i q/64).
@@ -537,7 +754,7 @@ __device__ __forceinline__ void eval_body(const TileDev& T, const JobDev& J, rea
       if (ty < T.eh && tx < T.ew) {
         const int gy = T.ey + ty, gx = T.ex + tx;
         const size_t gi = (size_t)gy * J.pitch + gx;
-        if (__ldg(J.mask + gi) != 0) {
+        if (__ldcg(J.mask + gi) != 0) {
           val[(size_t)ty * (CTA ? T.ew : T.vp) + tx] = g;  // CTA-wide executors: unpadded planes
           if (gx >= T.x && gx < T.x + T.w && gy >= T.y && gy < T.y + T.h) {
             J.out[gi] = to_u8(g);
@@ -760,7 +977,7 @@ template <class WS>
 __device__ __forceinline__ bool stage_fft32(const ExecArgs& a, int id, WS& sm, float2* zbuf, int lane,
                                             float2 (&x)[32], unsigned char* sbuf, int sbytes, float& rbar) {
   const ClassArgs& C = a.c[CLS_F32_32];
-  const int2 it = C.items[id];
+  const int2 it = __ldcg(C.items + id);
   copy_desc(&sm.T, a.tiles + it.x, lane, 32);
   __syncwarp();
   copy_desc(&sm.J, a.jobs + sm.T.job, lane, 32);
@@ -818,7 +1035,7 @@ __device__ __forceinline__ bool item_f32_32(const ExecArgs& a, int id, WarpSmem3
   // stage -> rows 32..63 (swizzled F x F buffer); TMA boxes in rows 0..31
   float rbar;
   if (!stage_fft32(a, id, sm, sm.Wd + 32 * 32, lane, x, reinterpret_cast<unsigned char*>(sm.Wd), 8192, rbar)) return false;
-  const int2 it = C.items[id];
+  const int2 it = __ldcg(C.items + id);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -939,7 +1156,7 @@ __device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem
   float2 x[32];
   float rbar;
   if (!stage_fft32(a, id, sm, zbuf, lane, x, reinterpret_cast<unsigned char*>(sm.Wt) + 8192, 35 * 32 * 16 - 8192, rbar)) return false;
-  const int2 it = C.items[id];
+  const int2 it = __ldcg(C.items + id);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1090,7 +1307,7 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
   if (!stage_fft32(a, id, sm, sm.Wd, lane, x, kTma ? reinterpret_cast<unsigned char*>(sm.Wd) + 8192 : nullptr,
                    kTma ? 7680 : 0, rbar))
     return false;
-  const int2 it = C.items[id];
+  const int2 it = __ldcg(C.items + id);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1223,17 +1440,35 @@ __global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32C>::valu
     return;
   }
   for (;;) {
-    const int id = queue_pop_warp(C, a.timeout_ns, lane);
+    const int id = a.server ? server_pop_warp(a, C, CLS_F32_32, lane) : queue_pop_warp(C, a.timeout_ns, lane);
     if (id < 0) break;
-    if (!run_item32<WS, U>(a, id, sm, tw, lane)) break;  // staging timed out: this warp stops
+    if (id & SRV_CMD_BIT) {  // a request joins the running executor
+      server_admit<false>(a, C, CLS_F32_32, id & ~SRV_CMD_BIT, lane, 32);
+      continue;
+    }
+    // cancelled: release only (decided once, by lane 0, for the whole warp)
+    const bool skip = a.server && __shfl_sync(0xffffffffu, lane == 0 ? (int)server_cancelled(a, C, id) : 0, 0);
+    if (skip) {
+      const int2 it = __ldcg(C.items + id);
+      copy_desc(&sm.T, a.tiles + it.x, lane, 32);
+      __syncwarp();
+      copy_desc(&sm.J, a.jobs + sm.T.job, lane, 32);
+      __syncwarp();
+    } else if (!run_item32<WS, U>(a, id, sm, tw, lane)) {
+      break;  // staging timed out: this warp stops
+    }
     // value-plane stores before later blocks' TMA (asynchronous-proxy) reads
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __threadfence();
     __syncwarp();
-    const int2 it = C.items[id];
+    const int2 it = __ldcg(C.items + id);
     release_successors(a, C, sm.T, sm.J, it.y >> 16, it.y & 0xFFFF, lane, 32);
     __syncwarp();
-    if (lane == 0) atomicAdd(&C.q->n_done, 1);
+    if (lane == 0) {
+      atomicAdd(&C.q->n_done, 1);
+      if (a.server) server_block_done(a, sm.T.job);
+    }
+    __syncwarp();
   }
 }
 
@@ -1254,6 +1489,7 @@ struct alignas(16) CtaSmem64 {
   float red[NWB * 32];
   alignas(16) float4 xrec[2][NWB];  // per warp: (key bits, flat bits, Re R_u, Im R_u)
   int item;
+  int skip;  // server mode: the popped block's request is cancelled
   TileDev T;
   JobDev J;
 };
@@ -1264,7 +1500,7 @@ struct alignas(16) CtaSmem64 {
 template <int NT, class Sm>
 __device__ __forceinline__ float stage_fft64(const ExecArgs& a, int id, Sm& sm, float2* zbuf, int t) {
   const ClassArgs& C = a.c[CLS_F32_64];
-  const int2 it = C.items[id];
+  const int2 it = __ldcg(C.items + id);
   copy_desc(&sm.T, a.tiles + it.x, t, NT);
   __syncthreads();
   copy_desc(&sm.J, a.jobs + sm.T.job, t, NT);
@@ -1327,7 +1563,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   const ClassArgs& C = a.c[CLS_F32_64];
   float2* zbuf = ROWS == 128 ? sm.Wd + 64 * 64 : sm.Wd;
   const float rbar = stage_fft64<NT>(a, id, sm, zbuf, t);
-  const int2 it = C.items[id];
+  const int2 it = __ldcg(C.items + id);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1488,7 +1724,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
   float2* zbuf = sm.Wd;  // the FFT buffer is table rows 0..31
   float4* Wt = reinterpret_cast<float4*>(sm.Wd);
   const float rbar = stage_fft64<NT>(a, id, sm, zbuf, t);
-  const int2 it = C.items[id];
+  const int2 it = __ldcg(C.items + id);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1647,18 +1883,35 @@ __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS
   }
   for (;;) {
     if (t < 32) {
-      const int id = queue_pop_warp(C, a.timeout_ns, t);
-      if (t == 0) sm.item = id;
+      const int id = a.server ? server_pop_warp(a, C, CLS_F32_64, t) : queue_pop_warp(C, a.timeout_ns, t);
+      if (t == 0) {
+        sm.item = id;
+        sm.skip = a.server && id >= 0 && !(id & SRV_CMD_BIT) && server_cancelled(a, C, id);
+      }
     }
     __syncthreads();
     const int id = sm.item;
     if (id < 0) break;
-    run_item64<NWB, ROWS, U>(a, id, sm, t);
+    if (id & SRV_CMD_BIT) {  // a request joins the running executor
+      server_admit<true>(a, C, CLS_F32_64, id & ~SRV_CMD_BIT, t, NT);
+      continue;
+    }
+    if (sm.skip) {  // cancelled: release only (decided once, by thread 0)
+      const int2 it = __ldcg(C.items + id);
+      copy_desc(&sm.T, a.tiles + it.x, t, NT);
+      __syncthreads();
+      copy_desc(&sm.J, a.jobs + sm.T.job, t, NT);
+    } else {
+      run_item64<NWB, ROWS, U>(a, id, sm, t);
+    }
     __threadfence();
     __syncthreads();
-    const int2 it = C.items[id];
+    const int2 it = __ldcg(C.items + id);
     release_successors(a, C, sm.T, sm.J, it.y >> 16, it.y & 0xFFFF, t, NT);
-    if (t == 0) atomicAdd(&C.q->n_done, 1);
+    if (t == 0) {
+      atomicAdd(&C.q->n_done, 1);
+      if (a.server) server_block_done(a, sm.T.job);
+    }
     __syncthreads();
   }
 }
@@ -1709,7 +1962,7 @@ __device__ void fft_line_d(double2* x, int st, int n, int logn) {
 
 __device__ __forceinline__ void item_f64(const ExecArgs& a, int id, CtaSmemD& sm, int t) {
   const ClassArgs& C = a.c[CLS_F64];
-  const int2 it = C.items[id];
+  const int2 it = __ldcg(C.items + id);
   const TileDev T = a.tiles[it.x];
   const JobDev J = a.jobs[T.job];
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1839,7 +2092,7 @@ __global__ void __launch_bounds__(NT64) k_exec_f64(const __grid_constant__ ExecA
     item_f64(a, id, sm, t);
     __threadfence();
     __syncthreads();
-    const int2 it = C.items[id];
+    const int2 it = __ldcg(C.items + id);
     const TileDev T = a.tiles[it.x];
     const JobDev J = a.jobs[T.job];
     release_successors(a, C, T, J, it.y >> 16, it.y & 0xFFFF, t, NT64);
@@ -1906,23 +2159,11 @@ __global__ void k_deps(const __grid_constant__ ExecArgs a, int cls) {
   const ClassArgs& C = a.c[cls];
   const int n = min(C.q->n_items, C.cap);
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
-    const int2 it = C.items[id];
+    const int2 it = __ldcg(C.items + id);
     const TileDev T = a.tiles[it.x];
     const JobDev J = a.jobs[T.job];
     const int I = it.y >> 16, Jb = it.y & 0xFFFF;
-    int cnt = 0;
-    if (J.order != ORDER_INDEPENDENT) {
-      const int D = J.D;
-      const int64_t kx = order_key(J, I, Jb);
-      const int32_t* map = a.map + T.map_off;
-      for (int dI = -D; dI <= D; ++dI)
-        for (int dJ = -D; dJ <= D; ++dJ) {
-          const int I2 = I + dI, J2 = Jb + dJ;
-          if (I2 < 0 || I2 >= T.nby || J2 < 0 || J2 >= T.nbx) continue;
-          const int id2 = map[I2 * T.nbx + J2];
-          if (id2 >= 0 && order_key(J, I2, J2) < kx) ++cnt;
-        }
-    }
+    const int cnt = count_preds(J, T, a.map + T.map_off, I, Jb);
     C.cnt[id] = cnt;
     if (a.level_of) a.level_of[(size_t)cls * a.level_stride + id] =
         J.order == ORDER_PHASED ? (I % J.P) * J.P + (Jb % J.P) : 0;
