@@ -67,7 +67,7 @@ def parse():
                     help="oracle seconds per CPU-baseline leg (all cores, then one core)")
     ap.add_argument("--no-per-block", action="store_true", help="skip the per-block launch baseline")
     ap.add_argument("--arena-mb", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=600,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="measured requests of the serving leg (0 = skip)")
     ap.add_argument("--f64-warps", type=int, default=0, choices=[0, 2, 4, 5, 6, 8])
     ap.add_argument("--f32-layout", type=int, default=0, choices=[0, 1, 2, 3, 4])
@@ -265,63 +265,94 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # serving leg: Poisson arrivals into the continuous-batching server
 # ---------------------------------------------------------------------------
-def serve_leg(fse, device, n_measured, n_warm=100, pool_size=16, rate_hz=200.0):
-    """Requests follow the serving workload: Poisson arrivals (mean 200/s),
-    areas log-uniform in 128^2 .. 7680x4320, 1-30 % of the 8x8 blocks lost,
-    K in 100..200.  Images come from a pool of pool_size seeded requests,
-    reused cyclically; arrival times are drawn for every request."""
+def serve_leg(fse, device, n_measured, n_warm=50, rate_hz=200.0, n_capacity=300, lookahead=48):
+    """The serving workload through the continuous-batching server.
+
+    Poisson leg: n_warm + n_measured fresh requests (each drawn anew: size
+    log-uniform 128^2 .. 7680x4320, 1-30 % of the 8x8 blocks lost, K in
+    100..200, pixels cropped from two seeded 7680x4320 images at a drawn
+    position) arrive at their drawn times (mean 200/s); a producer thread builds
+    each request's buffers ahead of its arrival.  Reported: achieved request
+    rate, served lost blocks/s and Mpix/s, p50/p99 latency (submit ->
+    completion seen by the server).
+    Capacity leg: n_capacity further fresh requests, built before timing,
+    submitted back to back; served lost blocks/s and Mpix/s from the first
+    submit to the last completion."""
+    import queue as _queue
     import threading
     from paper_2207_00238_gb300 import synth
-    stream = synth.serving_stream(n_requests=pool_size)
-    pool = [job for _, job in stream]
-    rng = synth.Rng(synth.SEED_BASE + 55)
+    textures = synth.serving_textures()
     n = n_warm + n_measured
-    gaps = -np.log1p(-rng.uniform(n)) / rate_hz
-    arrivals = np.cumsum(gaps)
+    specs = list(synth.serving_requests(textures, n_requests=n, rate_hz=rate_hz))
     ctx = fse.Context(device, arena_bytes=256 << 20)
-    srv = fse.Server(ctx, arena_bytes=24 << 30, max_queue=4096, max_resident=256, max_batch=16)
-    outs = {}
-    tickets = []
-    done_count = [0]
+    ctx.set_option(fse.OPT_SERVER_CLASSES, 2)  # every serving request is F = 64
+    srv = fse.Server(ctx, arena_bytes=24 << 30, max_queue=4096, max_resident=256)
+    try:
+        ready = _queue.Queue(maxsize=lookahead)
 
-    def waiter():
-        i = 0
-        while i < n:
-            if i >= len(tickets):
-                time.sleep(0.0005)
-                continue
-            srv.wait(tickets[i], timeout_ms=120000)
-            outs.pop(i, None)
-            i += 1
-        done_count[0] = i
+        def producer():
+            for _, spec in specs:
+                ready.put(synth.materialise(textures, spec))
 
-    th = threading.Thread(target=waiter)
-    th.start()
-    t0 = time.perf_counter()
-    t_meas = None
-    for k in range(n):
-        now = time.perf_counter() - t0
-        if arrivals[k] > now:
-            time.sleep(arrivals[k] - now)
-        if k == n_warm:
-            t_meas = time.perf_counter()
-        job = pool[k % pool_size]
-        out = np.empty_like(job["image"])
-        outs[k] = out
-        tickets.append(srv.submit(job["image"], job["mask"], out, job["params"]))
-    th.join()
-    t_end = time.perf_counter()
-    lat = srv.latencies()[-n_measured:]
-    srv.close()
-    ctx.close()
-    px = sum(pool[k % pool_size]["image"].size for k in range(n_warm, n))
-    wall = t_end - t_meas
-    return {"requests": n_measured, "warmup_requests": n_warm, "offered_rate_hz": rate_hz,
-            "achieved_rate_hz": n_measured / wall, "mpix_per_s": px / wall / 1e6,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3),
-            "pool": f"{pool_size} seeded requests reused cyclically; Poisson arrivals drawn per request",
-            "lanes": 4}
+        tickets = [None] * n
+        lat = np.zeros(n)
+        got = threading.Semaphore(0)
+
+        def waiter():
+            for i in range(n):
+                got.acquire()
+                lat[i] = srv.wait(tickets[i], timeout_ms=300000)["exec_ms"] * 1e-3  # submit -> done
+
+        pt = threading.Thread(target=producer, daemon=True)
+        wt = threading.Thread(target=waiter, daemon=True)
+        pt.start()
+        wt.start()
+        t0 = time.perf_counter()
+        lag = 0.0
+        t_meas = None
+        for k, (arr, _) in enumerate(specs):
+            job = ready.get()
+            now = time.perf_counter() - t0
+            if arr > now:
+                time.sleep(arr - now)
+            else:
+                lag = max(lag, now - arr) if k >= n_warm else lag
+            if k == n_warm:
+                t_meas = time.perf_counter()
+            out = np.empty_like(job["image"])
+            tickets[k] = srv.submit(job["image"], job["mask"], out, job["params"])
+            got.release()
+        wt.join()
+        t_end = time.perf_counter()
+        lat = lat[n_warm:]
+        meas = [sp for _, sp in specs[n_warm:]]
+        px = sum(sp["W"] * sp["H"] for sp in meas)
+        blocks = sum(int(sp["flags"].sum()) for sp in meas)
+        wall = t_end - t_meas
+        poisson = {"requests": n_measured, "warmup_requests": n_warm, "offered_rate_hz": rate_hz,
+                   "achieved_rate_hz": n_measured / wall, "lost_blocks_per_s": blocks / wall,
+                   "mpix_per_s": px / wall / 1e6, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                   "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                   "max_submit_lag_ms": lag * 1e3}
+        # capacity: requests submitted back to back
+        cap_specs = [sp for _, sp in synth.serving_requests(textures, n_requests=n_capacity,
+                                                            seed=synth.SEED_BASE + 8)]
+        jobs = [synth.materialise(textures, sp) for sp in cap_specs]
+        outs = [np.empty_like(j["image"]) for j in jobs]
+        t0 = time.perf_counter()
+        tk = [srv.submit(j["image"], j["mask"], o, j["params"]) for j, o in zip(jobs, outs)]
+        lat = np.array([srv.wait(t, timeout_ms=300000)["exec_ms"] * 1e-3 for t in tk])
+        wall = time.perf_counter() - t0
+        capacity = {"requests": n_capacity,
+                    "lost_blocks_per_s": sum(int(sp["flags"].sum()) for sp in cap_specs) / wall,
+                    "mpix_per_s": sum(sp["W"] * sp["H"] for sp in cap_specs) / wall / 1e6,
+                    "seconds": wall, "p50_ms": float(np.percentile(lat, 50) * 1e3)}
+    finally:
+        srv.close()
+        ctx.close()
+    return {"poisson": poisson, "capacity": capacity,
+            "requests": "fresh per request: sizes, loss flags, K and crop position drawn; pixels "
+                        "cropped from two seeded 7680x4320 images; F=64, B=16, b=8"}
 
 
 # ---------------------------------------------------------------------------

@@ -346,7 +346,10 @@ int fse_poll(fse_server_t* srv, uint64_t ticket, int32_t* state);
 int fse_cancel(fse_server_t* srv, uint64_t ticket);
 /* Waits up to timeout_ms (< 0: no limit) for completion; st may be NULL.
  * Returns FSE_OK, the request's error status, FSE_ETIMEOUT or FSE_ENOTFOUND.
- * A completed ticket is forgotten after fse_wait returns FSE_OK for it. */
+ * A completed ticket is forgotten after fse_wait returns FSE_OK for it.
+ * For a server request st holds jobs = 1, pixels, device_ms = milliseconds
+ * from admission to completion and exec_ms = milliseconds from fse_submit to
+ * completion (the request's latency); the other fields are 0. */
 int fse_wait(fse_server_t* srv, uint64_t ticket, int32_t timeout_ms, fse_stats_t* st);
 /* Per-request latency record of the last completed tickets (seconds from
  * submit to done), newest last; returns how many were written. */

@@ -78,6 +78,13 @@ __device__ __forceinline__ T_ ldcg_struct(const T_* p) {
   return v;
 }
 
+// Read of job data: through the read-only cache in a batch call (everything
+// was written before the launch), through L2 in server mode (coh).
+template <typename T_>
+__device__ __forceinline__ T_ ld_in(const T_* p, bool coh) {
+  return coh ? __ldcg(p) : __ldg(p);
+}
+
 // Barrier of a block's thread group: the CTA, or one warp.
 template <bool CTA>
 __device__ __forceinline__ void bar() {
@@ -137,7 +144,8 @@ __device__ int queue_pop_warp(const ClassArgs& C, int64_t timeout_ns, int lane) 
 // Lost predecessors of block (I, Jb) inside its dependency window: under
 // PHASED the window's lost blocks of lower phase, under RASTER the earlier
 // ones, under INDEPENDENT none.
-__device__ __forceinline__ int count_preds(const JobDev& J, const TileDev& T, const int32_t* map, int I, int Jb) {
+__device__ __forceinline__ int count_preds(const JobDev& J, const TileDev& T, const int32_t* map, int I, int Jb,
+                                           bool coh) {
   if (J.order == ORDER_INDEPENDENT) return 0;
   const int D = J.D;
   const int64_t kx = order_key(J, I, Jb);
@@ -146,7 +154,7 @@ __device__ __forceinline__ int count_preds(const JobDev& J, const TileDev& T, co
     for (int dJ = -D; dJ <= D; ++dJ) {
       const int I2 = I + dI, J2 = Jb + dJ;
       if (I2 < 0 || I2 >= T.nby || J2 < 0 || J2 >= T.nbx) continue;
-      const int id2 = __ldcg(map + I2 * T.nbx + J2);
+      const int id2 = ld_in(map + I2 * T.nbx + J2, coh);
       if (id2 >= 0 && order_key(J, I2, J2) < kx) ++cnt;
     }
   return cnt;
@@ -163,7 +171,7 @@ __device__ __forceinline__ void release_successors(const ExecArgs& a, const Clas
   for (int pos = t; pos < wd * wd; pos += nthr) {
     const int I2 = I + pos / wd - D, J2 = Jb + pos % wd - D;
     if (I2 < 0 || I2 >= T.nby || J2 < 0 || J2 >= T.nbx) continue;
-    const int id2 = __ldcg(map + I2 * T.nbx + J2);
+    const int id2 = ld_in(map + I2 * T.nbx + J2, a.server != 0);
     if (id2 < 0 || order_key(J, I2, J2) <= kx) continue;
     if (atomicSub(&C.cnt[id2], 1) == 1) {
       __threadfence();
@@ -332,7 +340,7 @@ __device__ void server_admit(const ExecArgs& a, const ClassArgs& C, int cls, int
     const int nb = T.nbx * T.nby;
     for (int k = t; k < nb; k += nthr) {
       const int id = __ldcg(map + k);
-      if (id >= 0) C.cnt[id] = count_preds(J, T, map, k / T.nbx, k % T.nbx);
+      if (id >= 0) C.cnt[id] = count_preds(J, T, map, k / T.nbx, k % T.nbx, true);
     }
   }
   __threadfence();
@@ -347,7 +355,7 @@ __device__ void server_admit(const ExecArgs& a, const ClassArgs& C, int cls, int
     const int nb = T.nbx * T.nby;
     for (int k = t; k < nb; k += nthr) {
       const int id = __ldcg(map + k);
-      if (id >= 0 && count_preds(J, T, map, k / T.nbx, k % T.nbx) == 0) queue_push(C, id);
+      if (id >= 0 && count_preds(J, T, map, k / T.nbx, k % T.nbx, true) == 0) queue_push(C, id);
     }
   }
   bar<CTA>();
@@ -373,8 +381,8 @@ __device__ __forceinline__ int swz(int m, int n) {
   return m * F + (n ^ (m & (F - 1)));
 }
 
-template <int F, typename real, typename real2>
-__device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J, const real* val,
+template <int F, bool COH, typename real, typename real2>
+__device__ __forceinline__ void stage_support_impl(const TileDev& T, const JobDev& J, const real* val,
                                               int I, int Jb, real2* zbuf, int t, int nthr) {
   const int S = J.S;
   const int oy = I * J.b - J.B, ox = Jb * J.b - J.B;
@@ -410,9 +418,9 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
       in[u] = col_in && m < S && ty >= 0 && ty < eh;
       const size_t gi = in[u] ? g0 + (size_t)ty * pitch + tx : g0;
       const size_t vi = in[u] ? (size_t)ty * vp + tx : 0;
-      wi[u] = __ldcg(wiso + (m < S ? m * S + n : n));
-      mk[u] = __ldcg(mask + gi);
-      px[u] = __ldcg(image + gi);
+      wi[u] = ld_in(wiso + (m < S ? m * S + n : n), COH);
+      mk[u] = ld_in(mask + gi, COH);
+      px[u] = ld_in(image + gi, COH);
       v[u] = __ldcg(val + vi);
     }
 #pragma unroll
@@ -435,6 +443,17 @@ __device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J,
       zbuf[swz<F>(m, n)] = z;
     }
   }
+}
+
+// The staging loop in its batch form (read-only cache) or its server form
+// (L2), chosen once per block.
+template <int F, typename real, typename real2>
+__device__ __forceinline__ void stage_support(const TileDev& T, const JobDev& J, const real* val, int I, int Jb,
+                                              real2* zbuf, int t, int nthr, bool coh) {
+  if (coh)
+    stage_support_impl<F, true, real, real2>(T, J, val, I, Jb, zbuf, t, nthr);
+  else
+    stage_support_impl<F, false, real, real2>(T, J, val, I, Jb, zbuf, t, nthr);
 }
 
 // ---------------------------------------------------------------------------
@@ -551,7 +570,7 @@ __device__ __forceinline__ void stage_from_boxes(const TileDev& T, const JobDev&
     const int ty = oy + m;
     float wv = 0.f, rv = 0.f;
     if (col_in && ty >= 0 && ty < T.eh) {
-      const float wi = __ldcg(wiso + m * S + n);
+      const float wi = __ldg(wiso + m * S + n);
       const int mk = smask[m * bw + dx8 + n];
       if (mk == 0) {
         wv = wi;
@@ -684,11 +703,11 @@ __device__ __forceinline__ void fft_reg(float2 (&x)[N]) {
 
 // Copies a descriptor into shared memory word by word (t of nthr threads).
 template <typename T_>
-__device__ __forceinline__ void copy_desc(T_* dst, const T_* src, int t, int nthr) {
+__device__ __forceinline__ void copy_desc(T_* dst, const T_* src, int t, int nthr, bool coh) {
   static_assert(sizeof(T_) % 4 == 0, "descriptor size");
   const int* s = reinterpret_cast<const int*>(src);
   int* d = reinterpret_cast<int*>(dst);
-  for (int i = t; i < (int)(sizeof(T_) / 4); i += nthr) d[i] = __ldcg(s + i);
+  for (int i = t; i < (int)(sizeof(T_) / 4); i += nthr) d[i] = ld_in(s + i, coh);
 }
 
 // Second radix-2 step of a 64-point transform split over lanes l and l ^ 16:
@@ -715,7 +734,7 @@ __device__ __forceinline__ void fft64_combine(float2 (&x)[32], int h) {
 template <bool CTA, int C, typename real, typename real2>
 __device__ __forceinline__ void eval_body(const TileDev& T, const JobDev& J, real* val, int I, int Jb,
                                const int* coef_u, const real2* coef_d, const real2* tw,
-                               real* red, int t, int nthr) {
+                               real* red, int t, int nthr, bool coh) {
   const int b = J.b, np = b * b, K = J.K, F = J.F, B = J.B;
   const int logF = F == 32 ? 5 : 6, tshift = 6 - logF;  // tw has 64 entries
   const int nsplit = np <= nthr ? nthr / np : 1;
@@ -754,7 +773,7 @@ __device__ __forceinline__ void eval_body(const TileDev& T, const JobDev& J, rea
       if (ty < T.eh && tx < T.ew) {
         const int gy = T.ey + ty, gx = T.ex + tx;
         const size_t gi = (size_t)gy * J.pitch + gx;
-        if (__ldcg(J.mask + gi) != 0) {
+        if (ld_in(J.mask + gi, coh) != 0) {
           val[(size_t)ty * (CTA ? T.ew : T.vp) + tx] = g;  // CTA-wide executors: unpadded planes
           if (gx >= T.x && gx < T.x + T.w && gy >= T.y && gy < T.y + T.h) {
             J.out[gi] = to_u8(g);
@@ -772,8 +791,8 @@ __device__ __forceinline__ void eval_body(const TileDev& T, const JobDev& J, rea
 template <bool CTA, typename real, typename real2>
 __device__ __forceinline__ void eval_and_write(const TileDev& T, const JobDev& J, real* val, int I, int Jb,
                                                const int* coef_u, const real2* coef_d, const real2* tw,
-                                               real* red, int t, int nthr) {
-  eval_body<CTA, 2, real, real2>(T, J, val, I, Jb, coef_u, coef_d, tw, red, t, nthr);
+                                               real* red, int t, int nthr, bool coh) {
+  eval_body<CTA, 2, real, real2>(T, J, val, I, Jb, coef_u, coef_d, tw, red, t, nthr, coh);
 }
 
 // CTA-wide executors: eight partial sums in a call of its own, so the
@@ -781,8 +800,8 @@ __device__ __forceinline__ void eval_and_write(const TileDev& T, const JobDev& J
 template <bool CTA, typename real, typename real2>
 __device__ __noinline__ void eval_and_write_call(const TileDev& T, const JobDev& J, real* val, int I,
                                                  int Jb, const int* coef_u, const real2* coef_d,
-                                                 const real2* tw, real* red, int t, int nthr) {
-  eval_body<CTA, 8, real, real2>(T, J, val, I, Jb, coef_u, coef_d, tw, red, t, nthr);
+                                                 const real2* tw, real* red, int t, int nthr, bool coh) {
+  eval_body<CTA, 8, real, real2>(T, J, val, I, Jb, coef_u, coef_d, tw, red, t, nthr, coh);
 }
 
 __device__ __forceinline__ void debug_record(const ExecArgs& a, int cls, int id, const TileDev& T,
@@ -977,10 +996,10 @@ template <class WS>
 __device__ __forceinline__ bool stage_fft32(const ExecArgs& a, int id, WS& sm, float2* zbuf, int lane,
                                             float2 (&x)[32], unsigned char* sbuf, int sbytes, float& rbar) {
   const ClassArgs& C = a.c[CLS_F32_32];
-  const int2 it = __ldcg(C.items + id);
-  copy_desc(&sm.T, a.tiles + it.x, lane, 32);
+  const int2 it = ld_in(C.items + id, a.server != 0);
+  copy_desc(&sm.T, a.tiles + it.x, lane, 32, a.server != 0);
   __syncwarp();
-  copy_desc(&sm.J, a.jobs + sm.T.job, lane, 32);
+  copy_desc(&sm.J, a.jobs + sm.T.job, lane, 32, a.server != 0);
   __syncwarp();
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -1006,7 +1025,7 @@ __device__ __forceinline__ bool stage_fft32(const ExecArgs& a, int id, WS& sm, f
     __syncwarp();
     if (lane == 0) sm.tma_ph = ph + 1;
   } else {
-    stage_support<32, float, float2>(T, J, val, I, Jb, zbuf, lane, 32);
+    stage_support<32, float, float2>(T, J, val, I, Jb, zbuf, lane, 32, a.server != 0);
   }
   __syncwarp();
   const float c = support_mean<32, 32>(zbuf, S, lane, nullptr);
@@ -1035,7 +1054,7 @@ __device__ __forceinline__ bool item_f32_32(const ExecArgs& a, int id, WarpSmem3
   // stage -> rows 32..63 (swizzled F x F buffer); TMA boxes in rows 0..31
   float rbar;
   if (!stage_fft32(a, id, sm, sm.Wd + 32 * 32, lane, x, reinterpret_cast<unsigned char*>(sm.Wd), 8192, rbar)) return false;
-  const int2 it = __ldcg(C.items + id);
+  const int2 it = ld_in(C.items + id, a.server != 0);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1122,7 +1141,7 @@ __device__ __forceinline__ bool item_f32_32(const ExecArgs& a, int id, WarpSmem3
   if (a.dbg_useq)
     for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
   eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
-                                       32);
+                                       32, a.server != 0);
   return true;
 }
 
@@ -1156,7 +1175,7 @@ __device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem
   float2 x[32];
   float rbar;
   if (!stage_fft32(a, id, sm, zbuf, lane, x, reinterpret_cast<unsigned char*>(sm.Wt) + 8192, 35 * 32 * 16 - 8192, rbar)) return false;
-  const int2 it = __ldcg(C.items + id);
+  const int2 it = ld_in(C.items + id, a.server != 0);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1267,7 +1286,7 @@ __device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem
   if (a.dbg_useq)
     for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
   eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
-                                       32);
+                                       32, a.server != 0);
   return true;
 }
 constexpr size_t SMEM32P = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32P);
@@ -1307,7 +1326,7 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
   if (!stage_fft32(a, id, sm, sm.Wd, lane, x, kTma ? reinterpret_cast<unsigned char*>(sm.Wd) + 8192 : nullptr,
                    kTma ? 7680 : 0, rbar))
     return false;
-  const int2 it = __ldcg(C.items + id);
+  const int2 it = ld_in(C.items + id, a.server != 0);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1396,7 +1415,7 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
   if (a.dbg_useq)
     for (int k = lane; k < K; k += 32) debug_useq(a, CLS_F32_32, id, k, sm.coef_u[k]);
   eval_and_write<false, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, tw, sm.red, lane,
-                                       32);
+                                       32, a.server != 0);
   return true;
 }
 constexpr size_t SMEM32R = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32R);
@@ -1449,10 +1468,10 @@ __global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32C>::valu
     // cancelled: release only (decided once, by lane 0, for the whole warp)
     const bool skip = a.server && __shfl_sync(0xffffffffu, lane == 0 ? (int)server_cancelled(a, C, id) : 0, 0);
     if (skip) {
-      const int2 it = __ldcg(C.items + id);
-      copy_desc(&sm.T, a.tiles + it.x, lane, 32);
+      const int2 it = ld_in(C.items + id, a.server != 0);
+      copy_desc(&sm.T, a.tiles + it.x, lane, 32, a.server != 0);
       __syncwarp();
-      copy_desc(&sm.J, a.jobs + sm.T.job, lane, 32);
+      copy_desc(&sm.J, a.jobs + sm.T.job, lane, 32, a.server != 0);
       __syncwarp();
     } else if (!run_item32<WS, U>(a, id, sm, tw, lane)) {
       break;  // staging timed out: this warp stops
@@ -1461,7 +1480,7 @@ __global__ void __launch_bounds__(NW32 * 32, std::is_same<WS, WarpSmem32C>::valu
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __threadfence();
     __syncwarp();
-    const int2 it = __ldcg(C.items + id);
+    const int2 it = ld_in(C.items + id, a.server != 0);
     release_successors(a, C, sm.T, sm.J, it.y >> 16, it.y & 0xFFFF, lane, 32);
     __syncwarp();
     if (lane == 0) {
@@ -1500,10 +1519,10 @@ struct alignas(16) CtaSmem64 {
 template <int NT, class Sm>
 __device__ __forceinline__ float stage_fft64(const ExecArgs& a, int id, Sm& sm, float2* zbuf, int t) {
   const ClassArgs& C = a.c[CLS_F32_64];
-  const int2 it = __ldcg(C.items + id);
-  copy_desc(&sm.T, a.tiles + it.x, t, NT);
+  const int2 it = ld_in(C.items + id, a.server != 0);
+  copy_desc(&sm.T, a.tiles + it.x, t, NT, a.server != 0);
   __syncthreads();
-  copy_desc(&sm.J, a.jobs + sm.T.job, t, NT);
+  copy_desc(&sm.J, a.jobs + sm.T.job, t, NT, a.server != 0);
   __syncthreads();
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
@@ -1512,7 +1531,7 @@ __device__ __forceinline__ float stage_fft64(const ExecArgs& a, int id, Sm& sm, 
   float* val = a.val_f + T.val_off;
   if (t == 0) debug_record(a, CLS_F32_64, id, T, it.x, I, Jb);
 
-  stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, NT);
+  stage_support<64, float, float2>(T, J, val, I, Jb, zbuf, t, NT, a.server != 0);
   __syncthreads();
   const float c = support_mean<64, NT>(zbuf, S, t, sm.red);
   // rows of w (r - c), 64-point lines on lane pairs (l, l ^ 16): half h transforms the samples
@@ -1563,7 +1582,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   const ClassArgs& C = a.c[CLS_F32_64];
   float2* zbuf = ROWS == 128 ? sm.Wd + 64 * 64 : sm.Wd;
   const float rbar = stage_fft64<NT>(a, id, sm, zbuf, t);
-  const int2 it = __ldcg(C.items + id);
+  const int2 it = ld_in(C.items + id, a.server != 0);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1699,7 +1718,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   if (a.dbg_useq)
     for (int k = t; k < K; k += NT) debug_useq(a, CLS_F32_64, id, k, sm.coef_u[k]);
   eval_and_write_call<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
-                                      NT);
+                                      NT, a.server != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1724,7 +1743,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
   float2* zbuf = sm.Wd;  // the FFT buffer is table rows 0..31
   float4* Wt = reinterpret_cast<float4*>(sm.Wd);
   const float rbar = stage_fft64<NT>(a, id, sm, zbuf, t);
-  const int2 it = __ldcg(C.items + id);
+  const int2 it = ld_in(C.items + id, a.server != 0);
   const TileDev& T = sm.T;
   const JobDev& J = sm.J;
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -1849,7 +1868,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
   if (a.dbg_useq)
     for (int k = t; k < K; k += NT) debug_useq(a, CLS_F32_64, id, k, sm.coef_u[k]);
   eval_and_write_call<true, float, float2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
-                                      NT);
+                                      NT, a.server != 0);
 }
 
 template <int NWB, int ROWS, int U>
@@ -1897,16 +1916,16 @@ __global__ void __launch_bounds__(NWB * 32, NWB == 8 ? 2 : (NWB == 2 ? 4 : (ROWS
       continue;
     }
     if (sm.skip) {  // cancelled: release only (decided once, by thread 0)
-      const int2 it = __ldcg(C.items + id);
-      copy_desc(&sm.T, a.tiles + it.x, t, NT);
+      const int2 it = ld_in(C.items + id, a.server != 0);
+      copy_desc(&sm.T, a.tiles + it.x, t, NT, a.server != 0);
       __syncthreads();
-      copy_desc(&sm.J, a.jobs + sm.T.job, t, NT);
+      copy_desc(&sm.J, a.jobs + sm.T.job, t, NT, a.server != 0);
     } else {
       run_item64<NWB, ROWS, U>(a, id, sm, t);
     }
     __threadfence();
     __syncthreads();
-    const int2 it = __ldcg(C.items + id);
+    const int2 it = ld_in(C.items + id, a.server != 0);
     release_successors(a, C, sm.T, sm.J, it.y >> 16, it.y & 0xFFFF, t, NT);
     if (t == 0) {
       atomicAdd(&C.q->n_done, 1);
@@ -1962,7 +1981,7 @@ __device__ void fft_line_d(double2* x, int st, int n, int logn) {
 
 __device__ __forceinline__ void item_f64(const ExecArgs& a, int id, CtaSmemD& sm, int t) {
   const ClassArgs& C = a.c[CLS_F64];
-  const int2 it = __ldcg(C.items + id);
+  const int2 it = ld_in(C.items + id, a.server != 0);
   const TileDev T = a.tiles[it.x];
   const JobDev J = a.jobs[T.job];
   const int I = it.y >> 16, Jb = it.y & 0xFFFF;
@@ -2058,7 +2077,7 @@ __device__ __forceinline__ void item_f64(const ExecArgs& a, int id, CtaSmemD& sm
     __syncthreads();
   }
   eval_and_write_call<true, double, double2>(T, J, val, I, Jb, sm.coef_u, sm.coef_d, sm.tw, sm.red, t,
-                                        NT64);
+                                        NT64, a.server != 0);
 }
 
 __global__ void __launch_bounds__(NT64) k_exec_f64(const __grid_constant__ ExecArgs a) {
@@ -2092,7 +2111,7 @@ __global__ void __launch_bounds__(NT64) k_exec_f64(const __grid_constant__ ExecA
     item_f64(a, id, sm, t);
     __threadfence();
     __syncthreads();
-    const int2 it = __ldcg(C.items + id);
+    const int2 it = ld_in(C.items + id, a.server != 0);
     const TileDev T = a.tiles[it.x];
     const JobDev J = a.jobs[T.job];
     release_successors(a, C, T, J, it.y >> 16, it.y & 0xFFFF, t, NT64);
@@ -2159,11 +2178,11 @@ __global__ void k_deps(const __grid_constant__ ExecArgs a, int cls) {
   const ClassArgs& C = a.c[cls];
   const int n = min(C.q->n_items, C.cap);
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
-    const int2 it = __ldcg(C.items + id);
+    const int2 it = ld_in(C.items + id, a.server != 0);
     const TileDev T = a.tiles[it.x];
     const JobDev J = a.jobs[T.job];
     const int I = it.y >> 16, Jb = it.y & 0xFFFF;
-    const int cnt = count_preds(J, T, a.map + T.map_off, I, Jb);
+    const int cnt = count_preds(J, T, a.map + T.map_off, I, Jb, false);
     C.cnt[id] = cnt;
     if (a.level_of) a.level_of[(size_t)cls * a.level_stride + id] =
         J.order == ORDER_PHASED ? (I % J.P) * J.P + (Jb % J.P) : 0;

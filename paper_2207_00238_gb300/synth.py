@@ -246,6 +246,82 @@ def serving_stream(seed=SEED_BASE + 5, n_requests=2200, rate_hz=200.0,
         yield t, dict(image=img, mask=mask, params=params(8, 16, 64, K))
 
 
+
+def burst_flags(nbx, nby, n_lost, rng, burst_frac=0.5):
+    """Vectorised lost-block flags for large grids: about ``burst_frac`` of the
+    n_lost blocks in runs of 2..8 along a block row (runs drawn at once, clipped
+    at the row end, overlaps merged), the rest isolated uniform picks among the
+    blocks still present.  Exactly min(n_lost, nbx*nby) flags are set."""
+    nb = nbx * nby
+    n_lost = min(int(n_lost), nb)
+    lost = np.zeros(nb, bool)
+    n_burst = int(round(n_lost * burst_frac))
+    if n_burst > 0:
+        runs = max(1, n_burst // 5)
+        start = rng.randint(runs, 0, nb - 1)
+        L = rng.randint(runs, 2, 8)
+        r, c = np.divmod(start, nbx)
+        off = np.arange(8)
+        cc = c[:, None] + off[None, :]
+        ok = (off[None, :] < L[:, None]) & (cc < nbx)
+        k = np.unique((r[:, None] * nbx + cc)[ok])
+        if len(k) > n_burst:  # drop a random excess, not the last rows
+            k = k[np.argpartition(rng.u64(len(k)), n_burst - 1)[:n_burst]]
+        lost[k] = True
+    rest = n_lost - int(lost.sum())
+    if rest > 0:
+        free = np.flatnonzero(~lost)
+        # distinct picks by sorting random keys (vectorised; no Python loop)
+        pick = np.argpartition(rng.u64(len(free)), rest - 1)[:rest] if rest < len(free) else np.arange(len(free))
+        lost[free[pick]] = True
+    return lost.reshape(nby, nbx)
+
+
+def expand_flags(flags, b, W, H):
+    """Pixel mask (u8, 1 = lost) of a b x b block-flag grid, cropped to H x W."""
+    return np.ascontiguousarray(np.repeat(np.repeat(flags.astype(np.uint8), b, 0), b, 1)[:H, :W])
+
+
+def serving_textures(n=2, seed=SEED_BASE + 6, W=7680, H=4320):
+    """Large seeded images from which fresh serving requests take their content."""
+    return [image(W, H, Rng(seed * 1009 + i), structure=True) for i in range(n)]
+
+
+def serving_requests(textures, n_requests=2000, seed=SEED_BASE + 7, rate_hz=200.0,
+                     min_area=128 * 128, max_area=7680 * 4320):
+    """Fresh requests of the serving workload, drawn per request like
+    serving_stream (Poisson arrivals, log-uniform area, aspect U(1, 16/9), loss
+    U(1 %, 30 %) of the 8x8 blocks, isolated/burst 50/50, K in 100..200, F=64,
+    B=16).  The pixels of each request are a crop, at a position drawn per
+    request, of one of ``textures`` (so generating a request costs a copy, not
+    a synthesis); its block flags are drawn fresh.  Yields (arrival_s, spec)
+    with spec = dict(tex, x0, y0, W, H, flags, K): materialise() turns it into
+    a job."""
+    rng = Rng(seed)
+    t = 0.0
+    TH, TW = textures[0].shape
+    for k in range(n_requests):
+        t += -math.log1p(-rng.uniform(1)[0]) / rate_hz
+        area = math.exp(rng.uniform(1, math.log(min_area), math.log(max_area))[0])
+        aspect = rng.uniform(1, 1.0, 16.0 / 9.0)[0]
+        W = min(TW, max(16, int(round(math.sqrt(area * aspect)))))
+        H = min(TH, max(16, int(round(math.sqrt(area / aspect)))))
+        rate = rng.uniform(1, 0.01, 0.30)[0]
+        K = int(rng.randint(1, 100, 200)[0])
+        ti = int(rng.randint(1, 0, len(textures) - 1)[0])
+        x0 = int(rng.randint(1, 0, TW - W)[0])
+        y0 = int(rng.randint(1, 0, TH - H)[0])
+        nbx, nby = (W + 7) // 8, (H + 7) // 8
+        flags = burst_flags(nbx, nby, max(1, int(round(rate * nbx * nby))), Rng(seed * 1000003 + k))
+        yield t, dict(tex=ti, x0=x0, y0=y0, W=W, H=H, flags=flags, K=K)
+
+
+def materialise(textures, spec):
+    """The job of a serving_requests spec: contiguous image crop, pixel mask."""
+    W, H = spec["W"], spec["H"]
+    img = np.ascontiguousarray(textures[spec["tex"]][spec["y0"]:spec["y0"] + H, spec["x0"]:spec["x0"] + W])
+    return dict(image=img, mask=expand_flags(spec["flags"], 8, W, H), params=params(8, 16, 64, spec["K"]))
+
 CONFIGS = {
     "plain_64": plain_64,
     "tiled_1024": tiled_1024,

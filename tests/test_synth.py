@@ -115,3 +115,35 @@ def test_deterministic():
     assert (a["image"] == b["image"]).all() and (a["mask"] == b["mask"]).all()
     c = synth.tiled_1024(seed=synth.SEED_BASE + 9, W=128, H=96, K=20, n_tiles=4)[0]
     assert not (a["image"] == c["image"]).all()
+
+
+def test_burst_flags_exact_count_and_runs():
+    for (nbx, nby, n) in ((40, 30, 1), (40, 30, 300), (40, 30, 1200), (7, 3, 21), (960, 540, 50000)):
+        f = synth.burst_flags(nbx, nby, n, synth.Rng(synth.SEED_BASE + nbx + n))
+        assert f.shape == (nby, nbx) and f.dtype == bool
+        assert int(f.sum()) == min(n, nbx * nby)
+    # at 10 % loss about half the lost blocks sit in horizontal runs of >= 2
+    f = synth.burst_flags(200, 100, 2000, synth.Rng(synth.SEED_BASE + 9))
+    left = np.zeros_like(f)
+    left[:, 1:] = f[:, :-1]
+    right = np.zeros_like(f)
+    right[:, :-1] = f[:, 1:]
+    in_run = f & (left | right)
+    assert 0.35 < in_run.sum() / f.sum() < 0.75
+
+
+def test_serving_requests_are_fresh_and_follow_the_workload():
+    tex = [synth.image(640, 480, synth.Rng(synth.SEED_BASE + 1), structure=True)]
+    items = list(synth.serving_requests(tex, n_requests=50, max_area=640 * 480))
+    t = np.array([a for a, _ in items])
+    assert (np.diff(t) > 0).all()
+    seen = set()
+    for _, spec in items:
+        job = synth.materialise(tex, spec)
+        H, W = job["image"].shape
+        assert job["mask"].shape == (H, W) and job["image"].flags["C_CONTIGUOUS"]
+        assert 100 <= job["params"]["K"] <= 200 and job["params"]["fft"] == 64
+        lost = job["mask"].reshape(-1).mean()
+        assert 0.0 < lost <= 0.31 + 64.0 / (W * H)
+        seen.add((spec["x0"], spec["y0"], W, H))
+    assert len(seen) == len(items)
