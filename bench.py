@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--no-tma", action="store_true", help="stage supports with plain loads")
     ap.add_argument("--no-graph", action="store_true", help="time direct launches instead of graph replay")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--class-launch", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="FSE_OPT_CLASS_LAUNCH (-1: library default / autotuned)")
     ap.add_argument("--study", default=None, choices=[None, "overlap", "tiling"],
                     help="run a study instead of the benchmark (one JSON line per result)")
     ap.add_argument("--order", default=None, choices=[None, "phased", "raster", "independent"],
@@ -524,6 +526,8 @@ def main():
         ctx.set_option(fse.OPT_TMA_STAGING, 0)
     if args.ctas_per_sm:
         ctx.set_option(fse.OPT_CTAS_PER_SM, args.ctas_per_sm)
+    if args.class_launch >= 0:
+        ctx.set_option(fse.OPT_CLASS_LAUNCH, args.class_launch)
     keep, cjobs, pix = [], [], 0
     for j in jobs:
         img = torch.from_numpy(j["image"]).to(dev)
@@ -535,7 +539,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     tuned = None
-    if not args.no_autotune and not args.f64_warps and not args.f32_layout and not args.ctas_per_sm and args.mode == "dag":
+    if (not args.no_autotune and not args.f64_warps and not args.f32_layout and not args.ctas_per_sm
+            and args.class_launch < 0 and args.mode == "dag"):
         trace = ctx.autotune(cjobs, stream=sptr, reps=3)
         tuned = describe_tuning(trace)
     # one counted pass: blocks per step, bin-iterations per step (per class)

@@ -25,6 +25,7 @@
 // with an error flag that the host reads; nothing traps.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <type_traits>
 
@@ -1293,17 +1294,19 @@ constexpr size_t SMEM32P = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32P);
 
 // ---------------------------------------------------------------------------
 // Run layout of the F = 32 executor: lane l owns column l and all 32 rows, as
-// the column layout does, but reads its rows in eight runs of four, each from
-// its own base row, so W needs only rows 0..2 repeated (35 rows, 8.75 KB per
+// the column layout does, but reads its rows in four runs of eight, each from
+// its own base row, so W needs only rows 0..6 repeated (39 rows, 9.75 KB per
 // warp) and the table overlays the FFT buffer.  Same arithmetic and keys as
 // the column layout; more warps fit on an SM.
 // ---------------------------------------------------------------------------
-// PAD = 3712: bytes 8192..15871 from Wd take the TMA support boxes.  The
+// PAD = 2688: bytes 8192..15871 from Wd take the TMA support boxes.  The
 // compact form (PAD = 16, layout 4) stages with plain loads only and fits
 // 8 CTAs of 2 warps per SM at 128 registers per thread.
+constexpr int RUN32 = 8;                // rows per run
+constexpr int ROWS32 = 32 + RUN32 - 1;  // table rows: 0..31, then 0..RUN32-2 again
 template <int PAD>
 struct alignas(128) WarpSmem32RT {
-  float2 Wd[35 * 32];  // W rows 0..31, rows 32..34 repeat rows 0..2; rows 0..31 double as FFT buffer
+  float2 Wd[ROWS32 * 32];  // W rows 0..31 and the repeated rows; rows 0..31 double as FFT buffer
   float2 coef_d[KMAX];
   int32_t coef_u[KMAX];
   float red[32];
@@ -1313,8 +1316,9 @@ struct alignas(128) WarpSmem32RT {
   TileDev T;
   JobDev J;
 };
-using WarpSmem32R = WarpSmem32RT<3712>;
+using WarpSmem32R = WarpSmem32RT<2688>;
 using WarpSmem32C = WarpSmem32RT<16>;
+static_assert(offsetof(WarpSmem32R, stage_pad) + 2688 >= 8192 + 7680, "TMA box area");
 
 template <int U, class WS>
 __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, const float2* tw,
@@ -1346,7 +1350,7 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
     const float2 z = x[j], z2 = x[j2];
     const float2 w = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
     sm.Wd[j * 32 + lane] = w;
-    if (j < 3) sm.Wd[(j + 32) * 32 + lane] = w;
+    if (j < RUN32 - 1) sm.Wd[(j + 32) * 32 + lane] = w;
     x[j] = make_float2(fmaf(rbar, w.x, 0.5f * (z.y + zm.y)), fmaf(rbar, w.y, 0.5f * (zm.x - z.x)));
     if (j2 != j) {
       const float2 w2 = make_float2(0.5f * (z2.x + zm2.x), 0.5f * (z2.y - zm2.y));
@@ -1388,9 +1392,9 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
     st_shared_if(lane == 0, &sm.coef_d[iter], make_float2(dx, dy));
     if (iter + 1 == K) break;
     const int d = (lane - u2) & 31;
-    const float2* wp[8];
+    const float2* wp[32 / RUN32];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) wp[q] = sm.Wd + ((4 * q - u1) & 31) * 32 + d;
+    for (int q = 0; q < 32 / RUN32; ++q) wp[q] = sm.Wd + ((RUN32 * q - u1) & 31) * 32 + d;
     const float ndx = -dx, ndy = -dy;
     bq[0] = bq[1] = 0u;
     static_for<0, 16>([&](auto h) {
@@ -1398,7 +1402,7 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
       float e[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const float2 w = wp[(j + k) >> 2][((j + k) & 3) * 32];
+        const float2 w = wp[(j + k) / RUN32][((j + k) % RUN32) * 32];
         float rx = fmaf(ndx, w.x, R[j + k].x);
         rx = fmaf(dy, w.y, rx);
         float ry = fmaf(ndx, w.y, R[j + k].y);
@@ -1420,6 +1424,7 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
 }
 constexpr size_t SMEM32R = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32R);
 constexpr size_t SMEM32C = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32C);
+static_assert(8 * (SMEM32C + 1024) <= 228 * 1024, "layout 4: 8 CTAs per SM");
 
 template <class WS, int U>
 __device__ __forceinline__ bool run_item32(const ExecArgs& a, int id, WS& sm, const float2* tw, int lane) {
