@@ -78,16 +78,32 @@ int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int 
   c->exec_mode = FSE_EXEC_DAG;
   c->use_graph = 0;
   int ran = 0;
-  // median iteration-kernel time of `reps` runs after one warm-up; trace rows
-  // (class or -1 for the class launch order, layout*10 + unroll or order code,
-  // ctas per SM, milliseconds)
+  // median time of `reps` runs after one warm-up: of the class's own
+  // persistent kernel when tuning a class (its start and end events, so the
+  // other classes add no noise), of all iteration kernels for the class launch
+  // order.  Trace rows: (class or -1 for the class launch order,
+  // layout*10 + unroll or order code, ctas per SM, milliseconds)
+  const int saved_timing = c->kernel_timing;
+  c->kernel_timing = 1;
   auto time_cfg = [&](int cls, int code, int ctas, double* ms_out) -> int {
+    constexpr size_t per_call = 2 + 2 * MAX_CLS;
     std::vector<double> ms;
     for (int r = 0; r < reps + 1; ++r) {
       fse_stats_t stt;
+      const size_t used = c->tev_used;
       int rc = run_batch(c, jobs, n, st, &stt, 0);
       if (rc) return rc;
-      if (r > 0) ms.push_back(stt.exec_ms);
+      double v = stt.exec_ms;
+      if (cls >= 0 && c->tev_used == used + per_call) {
+        float f = 0.f;
+        if (cudaEventElapsedTime(&f, c->tev[used + 2 + 2 * cls], c->tev[used + 3 + 2 * cls]) == cudaSuccess)
+          v = f;
+      }
+      if (c->tev_used == used + per_call) {  // keep the autotuner's runs out of the timing record
+        c->tev_used = used;
+        c->tev_cls_mask.pop_back();
+      }
+      if (r > 0) ms.push_back(v);
     }
     std::sort(ms.begin(), ms.end());
     *ms_out = ms[ms.size() / 2];
@@ -102,8 +118,7 @@ int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int 
   };
   int rc = FSE_OK;
   // per class: executor layout x K-loop unroll x persistent CTAs per SM, with
-  // the classes launched one after the other (the other classes run at their
-  // current setting and add a constant)
+  // the classes launched one after the other and the class timed alone
   const int saved_conc = c->concurrent;
   c->concurrent = 0;
   struct Cand { int lay, un, ctas_span; };
@@ -162,6 +177,7 @@ int autotune(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, int 
   }
   c->exec_mode = saved_mode;
   c->use_graph = saved_graph;
+  c->kernel_timing = saved_timing;
   c->graph_jobs.clear();
   if (rc) return rc;
   tune_save(c);

@@ -196,6 +196,8 @@ static int context_init(Context** out, int device, size_t arena_bytes, char* ali
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev3);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_host_free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_graph_done, cudaEventDisableTiming);
   for (int k = 0; k < MAX_CLS && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&c->cls_stream[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming);
@@ -234,9 +236,13 @@ int context_create_alias(Context** out, int device, char* arena, size_t arena_by
 void context_destroy(Context* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  cudaDeviceSynchronize();  // no queued copy may still read the staging buffers
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->arena && c->owns_arena) cudaFree(c->arena);
   if (c->host_buf) cudaFreeHost(c->host_buf);
+  if (c->graph_host_buf) cudaFreeHost(c->graph_host_buf);
+  if (c->ev_host_free) cudaEventDestroy(c->ev_host_free);
+  if (c->ev_graph_done) cudaEventDestroy(c->ev_graph_done);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->ev2) cudaEventDestroy(c->ev2);
@@ -251,18 +257,20 @@ void context_destroy(Context* c) {
   delete c;
 }
 
-static int ensure_host_buf(Context* c, size_t bytes) {
-  if (bytes <= c->host_cap) return FSE_OK;
-  if (c->host_buf) cudaFreeHost(c->host_buf);
-  c->host_buf = nullptr;
-  c->host_cap = 0;
+// Grows a pinned staging buffer; the caller has made sure that no queued copy
+// still reads it.
+static int ensure_pinned(char** buf, size_t* cap_io, size_t bytes) {
+  if (bytes <= *cap_io) return FSE_OK;
+  if (*buf) cudaFreeHost(*buf);
+  *buf = nullptr;
+  *cap_io = 0;
   const size_t cap = align_up(std::max(bytes, (size_t)1 << 20), 1 << 16);
-  cudaError_t e = cudaMallocHost(&c->host_buf, cap);
+  cudaError_t e = cudaMallocHost(buf, cap);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(FSE_ENOMEM, "pinned host buffer of %zu bytes", cap);
   }
-  c->host_cap = cap;
+  *cap_io = cap;
   return FSE_OK;
 }
 
@@ -515,7 +523,12 @@ int exec_grid(Context* c, int k) {
 static int enqueue(Context* c, const Plan& P, const ExecArgs& a, cudaStream_t st, int* nl,
                    bool timed) {
   int launches = 0;
-  FSE_CUDA(cudaMemcpyAsync(c->arena + P.o_jobs, c->host_buf, P.upload_bytes, cudaMemcpyHostToDevice, st));
+  const char* src = c->capturing ? c->graph_host_buf : c->host_buf;
+  FSE_CUDA(cudaMemcpyAsync(c->arena + P.o_jobs, src, P.upload_bytes, cudaMemcpyHostToDevice, st));
+  if (!c->capturing) {
+    FSE_CUDA(cudaEventRecord(c->ev_host_free, st));
+    c->host_buf_busy = true;
+  }
   if (P.ff_end > P.ff_begin) FSE_CUDA(cudaMemsetAsync(c->arena + P.ff_begin, 0xFF, P.ff_end - P.ff_begin, st));
   FSE_CUDA(cudaMemsetAsync(c->arena + P.zero_begin, 0, P.zero_end - P.zero_begin, st));
   if (c->debug && P.o_dbg_useq < P.total)
@@ -652,17 +665,25 @@ int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse
   if (rc) return rc;
   if (stats) memset(stats, 0, sizeof(*stats));
   if (n == 0) return FSE_OK;
-  // host tables -> pinned staging buffer
-  rc = ensure_host_buf(c, P.upload_bytes);
-  if (rc) return rc;
-  memset(c->host_buf, 0, P.upload_bytes);
-  memcpy(c->host_buf, P.jobs.data(), sizeof(JobDev) * n);
-  memcpy(c->host_buf + (P.o_tiles - P.o_jobs), P.tiles.data(), sizeof(TileDev) * P.tiles.size());
-  memcpy(c->host_buf + (P.o_wf - P.o_jobs), P.wf.data(), sizeof(float) * P.wf.size());
-  memcpy(c->host_buf + (P.o_wd - P.o_jobs), P.wd.data(), sizeof(double) * P.wd.size());
-  memcpy(c->host_buf + (P.o_tmap - P.o_jobs), P.maps.data(), sizeof(CUtensorMap) * P.maps.size());
-  const ExecArgs a = make_args(c, P);
   const bool timed = stats != nullptr;
+  const bool replay = c->exec_mode != FSE_EXEC_PER_BLOCK && c->use_graph && !timed && same_plan(c, P, jobs, n);
+  if (!replay) {
+    // host tables -> pinned staging buffer, once the previous call's copy out
+    // of it has run (a replayed graph copies from its own buffer instead)
+    if (c->host_buf_busy) {
+      FSE_CUDA(cudaEventSynchronize(c->ev_host_free));
+      c->host_buf_busy = false;
+    }
+    rc = ensure_pinned(&c->host_buf, &c->host_cap, P.upload_bytes);
+    if (rc) return rc;
+    memset(c->host_buf, 0, P.upload_bytes);
+    memcpy(c->host_buf, P.jobs.data(), sizeof(JobDev) * n);
+    memcpy(c->host_buf + (P.o_tiles - P.o_jobs), P.tiles.data(), sizeof(TileDev) * P.tiles.size());
+    memcpy(c->host_buf + (P.o_wf - P.o_jobs), P.wf.data(), sizeof(float) * P.wf.size());
+    memcpy(c->host_buf + (P.o_wd - P.o_jobs), P.wd.data(), sizeof(double) * P.wd.size());
+    memcpy(c->host_buf + (P.o_tmap - P.o_jobs), P.maps.data(), sizeof(CUtensorMap) * P.maps.size());
+  }
+  const ExecArgs a = make_args(c, P);
   if (timed) FSE_CUDA(cudaEventRecord(c->ev0, st));
   int launches = 0;
   int replayed = 0;
@@ -674,11 +695,19 @@ int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse
     if (rc) return rc;
     if (timed) FSE_CUDA(cudaEventRecord(c->ev3, st));
   } else if (c->use_graph && !timed) {
-    if (same_plan(c, P, jobs, n)) {
+    if (replay) {
       replayed = 1;
     } else {
-      if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+      if (c->graph_exec) {
+        // its copy node reads graph_host_buf, which is about to be rewritten
+        if (c->graph_launched) FSE_CUDA(cudaEventSynchronize(c->ev_graph_done));
+        cudaGraphExecDestroy(c->graph_exec);
+      }
       c->graph_exec = nullptr;
+      c->graph_launched = false;
+      rc = ensure_pinned(&c->graph_host_buf, &c->graph_host_cap, P.upload_bytes);
+      if (rc) return rc;
+      memcpy(c->graph_host_buf, c->host_buf, P.upload_bytes);
       cudaGraph_t g;
       FSE_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       c->capturing = 1;
@@ -697,6 +726,8 @@ int run_batch(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st, fse
     }
     launches = c->graph_launches;
     FSE_CUDA(cudaGraphLaunch(c->graph_exec, st));
+    FSE_CUDA(cudaEventRecord(c->ev_graph_done, st));
+    c->graph_launched = true;
   } else {
     rc = enqueue(c, P, a, st, &launches, timed);
     if (rc) return rc;

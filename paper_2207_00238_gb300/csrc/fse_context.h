@@ -18,6 +18,16 @@ struct fse_context {
   bool owns_arena = true;
   char* host_buf = nullptr;  // pinned staging of the per-call tables
   size_t host_cap = 0;
+  // host_buf is rewritten by the next call only after the copy that reads it
+  // has run (the calls are asynchronous): ev_host_free follows that copy
+  cudaEvent_t ev_host_free = nullptr;
+  bool host_buf_busy = false;
+  // the captured graph's copy node reads graph_host_buf, which stays unchanged
+  // while the graph exists; ev_graph_done follows its last launch
+  char* graph_host_buf = nullptr;
+  size_t graph_host_cap = 0;
+  cudaEvent_t ev_graph_done = nullptr;
+  bool graph_launched = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   cudaStream_t cap_stream = nullptr;  // graph capture happens here, replay on the caller's stream
   // options

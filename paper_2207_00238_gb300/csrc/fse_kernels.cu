@@ -1096,15 +1096,15 @@ __device__ __forceinline__ bool item_f32_32(const ExecArgs& a, int id, WarpSmem3
   // key: energy bits with the low 5 bits replaced by 31 - row; equal keys go
   // to the lowest lane, i.e. the lowest flat index
   const uint32_t kmask = opaque(0xFFFFFFE0u);
-  uint32_t bq[2] = {0u, 0u};  // two independent max chains, three-input max
+  uint32_t bq[4] = {0u, 0u, 0u, 0u};  // four independent max chains, three-input max
   static_for<0, 16>([&](auto h) {
     constexpr int j = 2 * decltype(h)::value;
     const float e0 = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
     const float e1 = fmaf(R[j + 1].y, R[j + 1].y, R[j + 1].x * R[j + 1].x);
-    bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<31u - j>(e0, kmask),
+    bq[(j >> 1) & 3] = max3u(bq[(j >> 1) & 3], make_key<31u - j>(e0, kmask),
                              make_key<30u - j>(e1, kmask));
   });
-  uint32_t best = max(bq[0], bq[1]);
+  uint32_t best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
   for (int iter = 0; iter < K; ++iter) {
     const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
     const int u2 = __ffs(__ballot_sync(0xffffffffu, best == wbest)) - 1;
@@ -1119,7 +1119,7 @@ __device__ __forceinline__ bool item_f32_32(const ExecArgs& a, int id, WarpSmem3
     if (iter + 1 == K) break;
     const float2* wp = sm.Wd + (32 - u1) * 32 + ((lane - u2) & 31);
     const float ndx = -dx, ndy = -dy;
-    bq[0] = bq[1] = 0u;
+    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
     static_for<0, 16>([&](auto h) {
       constexpr int j = 2 * decltype(h)::value;
       float e[2];
@@ -1133,10 +1133,10 @@ __device__ __forceinline__ bool item_f32_32(const ExecArgs& a, int id, WarpSmem3
         R[j + k] = make_float2(rx, ry);
         e[k] = fmaf(ry, ry, rx * rx);
       }
-      bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<31u - j>(e[0], kmask),
+      bq[(j >> 1) & 3] = max3u(bq[(j >> 1) & 3], make_key<31u - j>(e[0], kmask),
                                make_key<30u - j>(e[1], kmask));
     });
-    best = max(bq[0], bq[1]);
+    best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
   }
   __syncwarp();
   if (a.dbg_useq)
@@ -1231,15 +1231,15 @@ __device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem
   const float gs = J.gamma_f / W0;
   // key: energy bits with the low 5 bits replaced by 31 - l, l = 2 pi + c
   const uint32_t kmask = opaque(~31u);
-  uint32_t bq[2] = {0u, 0u};
+  uint32_t bq[4] = {0u, 0u, 0u, 0u};
   static_for<0, 16>([&](auto P) {
     constexpr int pi = decltype(P)::value;
     float2 e = __fmul2_rn(RX[pi], RX[pi]);
     e = __ffma2_rn(RY[pi], RY[pi], e);
-    bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+    bq[pi & 3] = max3u(bq[pi & 3], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
                        make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
   });
-  uint32_t best = max(bq[0], bq[1]);
+  uint32_t best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
 #pragma unroll U  // K-loop unroll factor (autotuned)
   for (int iter = 0; iter < K; ++iter) {
     const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
@@ -1265,7 +1265,7 @@ __device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem
 #pragma unroll
     for (int m = 0; m < 4; ++m) wp[m] = Wt + ((8 * m + 4 * h - u1) & 31) * 32 + d;
     const float2 ndx2 = make_float2(-dx, -dx), dy2 = make_float2(dy, dy), ndy2 = make_float2(-dy, -dy);
-    bq[0] = bq[1] = 0u;
+    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
     static_for<0, 16>([&](auto P) {
       constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
       const float4 w = wp[m][j * 32];
@@ -1278,10 +1278,10 @@ __device__ __forceinline__ bool item_f32_32p(const ExecArgs& a, int id, WarpSmem
       RY[pi] = ry;
       float2 e = __fmul2_rn(rx, rx);
       e = __ffma2_rn(ry, ry, e);
-      bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+      bq[pi & 3] = max3u(bq[pi & 3], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
                          make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
     });
-    best = max(bq[0], bq[1]);
+    best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
   }
   __syncwarp();
   if (a.dbg_useq)
@@ -1369,15 +1369,15 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
   // key: energy bits with the low 5 bits replaced by 31 - row; ties between
   // lanes (equal keys) go to the lowest lane, i.e. the lowest flat index
   const uint32_t kmask = opaque(0xFFFFFFE0u);
-  uint32_t bq[2] = {0u, 0u};
+  uint32_t bq[4] = {0u, 0u, 0u, 0u};
   static_for<0, 16>([&](auto h) {
     constexpr int j = 2 * decltype(h)::value;
     const float e0 = fmaf(R[j].y, R[j].y, R[j].x * R[j].x);
     const float e1 = fmaf(R[j + 1].y, R[j + 1].y, R[j + 1].x * R[j + 1].x);
-    bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<31u - j>(e0, kmask),
+    bq[(j >> 1) & 3] = max3u(bq[(j >> 1) & 3], make_key<31u - j>(e0, kmask),
                              make_key<30u - j>(e1, kmask));
   });
-  uint32_t best = max(bq[0], bq[1]);
+  uint32_t best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
 #pragma unroll U  // K-loop unroll factor (autotuned)
   for (int iter = 0; iter < K; ++iter) {
     const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
@@ -1396,7 +1396,7 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
 #pragma unroll
     for (int q = 0; q < 32 / RUN32; ++q) wp[q] = sm.Wd + ((RUN32 * q - u1) & 31) * 32 + d;
     const float ndx = -dx, ndy = -dy;
-    bq[0] = bq[1] = 0u;
+    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
     static_for<0, 16>([&](auto h) {
       constexpr int j = 2 * decltype(h)::value;
       float e[2];
@@ -1410,10 +1410,10 @@ __device__ __forceinline__ bool item_f32_32r(const ExecArgs& a, int id, WS& sm, 
         R[j + k] = make_float2(rx, ry);
         e[k] = fmaf(ry, ry, rx * rx);
       }
-      bq[(j >> 1) & 1] = max3u(bq[(j >> 1) & 1], make_key<31u - j>(e[0], kmask),
+      bq[(j >> 1) & 3] = max3u(bq[(j >> 1) & 3], make_key<31u - j>(e[0], kmask),
                                make_key<30u - j>(e[1], kmask));
     });
-    best = max(bq[0], bq[1]);
+    best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
   }
   __syncwarp();
   if (a.dbg_useq)
@@ -1660,15 +1660,15 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   // keys are resolved by the lowest flat index (lane ballot, then warps)
   const uint32_t kmask = opaque(~(uint32_t)(RPT - 1));
 
-  uint32_t bq[2] = {0u, 0u};
+  uint32_t bq[4] = {0u, 0u, 0u, 0u};
   static_for<0, RPT / 2>([&](auto h) {
     constexpr int i = 2 * decltype(h)::value;
     const float e0 = fmaf(R[i].y, R[i].y, R[i].x * R[i].x);
     const float e1 = fmaf(R[i + 1].y, R[i + 1].y, R[i + 1].x * R[i + 1].x);
-    bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i)>(e0, kmask),
+    bq[(i >> 1) & 3] = max3u(bq[(i >> 1) & 3], make_key<(uint32_t)(RPT - 1 - i)>(e0, kmask),
                              make_key<(uint32_t)(RPT - 2 - i)>(e1, kmask));
   });
-  uint32_t best = max(bq[0], bq[1]);
+  uint32_t best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
   for (int iter = 0; iter < K; ++iter) {
     {
       const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
@@ -1700,7 +1700,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     const float2* wp =
         sm.Wd + (ROWS == 128 ? r0 + 64 : (r0 < 0 ? r0 + 64 : r0)) * 64 + ((c - u2) & 63);
     const float ndx = -dx, ndy = -dy;
-    bq[0] = bq[1] = 0u;
+    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
     static_for<0, RPT / 2>([&](auto h) {
       constexpr int i = 2 * decltype(h)::value;
       float e[2];
@@ -1714,10 +1714,10 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
         R[i + k] = make_float2(rx, ry);
         e[k] = fmaf(ry, ry, rx * rx);
       }
-      bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i)>(e[0], kmask),
+      bq[(i >> 1) & 3] = max3u(bq[(i >> 1) & 3], make_key<(uint32_t)(RPT - 1 - i)>(e[0], kmask),
                                make_key<(uint32_t)(RPT - 2 - i)>(e[1], kmask));
     });
-    best = max(bq[0], bq[1]);
+    best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
   }
   __syncthreads();
   if (a.dbg_useq)
@@ -1805,15 +1805,15 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
   // thread's bin index (increasing with the flat index k1 * 64 + column);
   // equal keys are resolved by the lowest flat index (lane ballot, then warps)
   const uint32_t kmask = opaque(~31u);
-  uint32_t bq[2] = {0u, 0u};
+  uint32_t bq[4] = {0u, 0u, 0u, 0u};
   static_for<0, 16>([&](auto P) {
     constexpr int pi = decltype(P)::value;
     float2 e = __fmul2_rn(RX[pi], RX[pi]);
     e = __ffma2_rn(RY[pi], RY[pi], e);
-    bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+    bq[pi & 3] = max3u(bq[pi & 3], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
                        make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
   });
-  uint32_t best = max(bq[0], bq[1]);
+  uint32_t best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
 #pragma unroll U  // K-loop unroll factor (autotuned)
   for (int iter = 0; iter < K; ++iter) {
     {
@@ -1851,7 +1851,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
 #pragma unroll
     for (int m = 0; m < 4; ++m) wp[m] = Wt + ((16 * m + 4 * g - u1) & 63) * 64 + d;
     const float2 ndx2 = make_float2(-dx, -dx), dy2 = make_float2(dy, dy), ndy2 = make_float2(-dy, -dy);
-    bq[0] = bq[1] = 0u;
+    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
     static_for<0, 16>([&](auto P) {
       constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
       const float4 w = wp[m][j * 64];
@@ -1864,10 +1864,10 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
       RY[pi] = ry;
       float2 e = __fmul2_rn(rx, rx);
       e = __ffma2_rn(ry, ry, e);
-      bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+      bq[pi & 3] = max3u(bq[pi & 3], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
                          make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
     });
-    best = max(bq[0], bq[1]);
+    best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
   }
   __syncthreads();
   if (a.dbg_useq)

@@ -307,6 +307,66 @@ def test_graph_replay(ctx):
         ctx.set_option(fse.OPT_USE_GRAPH, 0)
 
 
+def test_back_to_back_calls_without_synchronisation(ctx):
+    """Calls return before their table upload has run.  Two different job
+    sets alternate on one stream with no synchronisation in between, each call
+    writing its own output buffers; then graph replays of one set alternate
+    with direct calls of the other.  Every call must see its own tables: a
+    staging buffer rewritten under a queued copy hands a call the other set's
+    tables, and its own outputs stay unwritten."""
+    import torch
+    dev = torch.device("cuda", 0)
+    R = 12
+    sets = [[_defects()], [_small_tiled(), synth.plain_64()[0]]]
+    refs = [run_gpu(ctx, js)[0] for js in sets]
+    outs, cjobs = [], []
+    for js in sets:
+        o_set, c_set = [], []
+        for j in js:
+            img = torch.from_numpy(j["image"]).to(dev)
+            msk = torch.from_numpy(j["mask"]).to(dev)
+            o = [torch.zeros_like(img) for _ in range(R)]
+            o_set.append((img, msk, o))
+            c_set.append([fse.make_job(img, msk, x, j["params"]) for x in o])
+        outs.append(o_set)
+        cjobs.append(c_set)
+
+    def call(si, r):
+        ctx.extrapolate([c[r] for c in cjobs[si]], stats=False)
+
+    def check(si, rs):
+        for k, (_, _, o) in enumerate(outs[si]):
+            for r in rs:
+                assert (o[r].cpu().numpy() == refs[si][k]["out"]).all(), (si, k, r)
+
+    torch.cuda.synchronize()
+    for r in range(R):  # direct launches, alternating sets
+        call(0, r)
+        call(1, r)
+    torch.cuda.synchronize()
+    check(0, range(R))
+    check(1, range(R))
+    for _, _, o in outs[0] + outs[1]:
+        for x in o:
+            x.zero_()
+    try:
+        ctx.set_option(fse.OPT_USE_GRAPH, 1)
+        call(0, 0)  # capture
+        torch.cuda.synchronize()
+        for r in range(R):  # replays of set 0 between direct calls of set 1
+            for _, _, o in outs[0]:
+                o[0].zero_()
+            ctx.set_option(fse.OPT_USE_GRAPH, 1)
+            call(0, 0)
+            ctx.set_option(fse.OPT_USE_GRAPH, 0)
+            call(1, r)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_option(fse.OPT_USE_GRAPH, 0)
+    check(0, [0])
+    check(1, range(R))
+
+
 def test_edge_cases(ctx, oracle_lib):
     rng = synth.Rng(synth.SEED_BASE + 40)
     img = synth.image(45, 37, rng)  # ragged: not a multiple of the block size
