@@ -37,10 +37,13 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 SMEM_BYTES_PER_CLK_SM = 128  # shared-memory bandwidth per SM per clock
 BYTES_PER_BIN_ITER = 8       # the gathered complex FP32 W(k-u) value
 
-# DRAM bytes per launch of the dominant kernel from an ncu capture of the same
-# workload, reported only while the kernel source is the one that was captured.
-CAPTURED_TRAFFIC = {"kernel_src_sha256_16": "036fbba36bddb834",
-                    "tiled_1024": 8307200, "defects_4k": 53262336 + 2532608}
+# DRAM bytes per launch of the dominant kernel (for the 256-image batch: per
+# step, both iteration kernels) from an ncu capture of the same workload,
+# reported only while the kernel source is the one that was captured.
+CAPTURED_TRAFFIC = {"kernel_src_sha256_16": "e35c0ed10cf14fda",
+                    "tiled_1024": 8327424, "defects_4k": 57336064 + 3376128,
+                    "batch_256": 5827400000 + 15154350000}
+CAPTURED_TRAFFIC_CLASS = {"batch_256": {"k_exec_f32_64": 5827400000, "k_exec_f32_32": 15154350000}}
 
 
 def captured_traffic(workload):
@@ -51,6 +54,12 @@ def captured_traffic(workload):
     if h != CAPTURED_TRAFFIC["kernel_src_sha256_16"]:
         return None
     return CAPTURED_TRAFFIC.get(workload)
+
+
+def captured_class_traffic(workload, kernel):
+    if captured_traffic(workload) is None:
+        return None
+    return CAPTURED_TRAFFIC_CLASS.get(workload, {}).get(kernel)
 
 
 def parse():
@@ -615,11 +624,13 @@ def main():
         ach_k = cls_bins[k] * BYTES_PER_BIN_ITER / (ms_k / 1000.0) / 1e9 if cls_bins[k] > 0 else None
         per_class[names[k]] = {"blocks_per_launch": cls_blocks[k], "bin_iterations_per_launch": cls_bins[k],
                                "kernel_ms": ms_k, "achieved": ach_k,
-                               "frac": ach_k / peak_gbs if ach_k else None}
+                               "frac": ach_k / peak_gbs if ach_k else None,
+                               "traffic": captured_class_traffic(args.workload, names[k])}
     roof = {"bound": "alu", "pipe": "shared-memory (LSU) pipe, 128 B/clk/SM",
             "achieved": achieved, "peak": peak_gbs, "unit": "GB/s", "frac": achieved / peak_gbs,
             "traffic": captured_traffic(args.workload),
-            "traffic_note": "DRAM bytes per launch (ncu); the kernel's bound is on chip",
+            "traffic_note": ("DRAM bytes per launch (ncu; for a mixed batch the sum over its class "
+                             "launches); the kernel's bound is on chip"),
             "kernel": "+".join(names[k] for k in (0, 1) if cls_blocks[k] > 0),
             "kernel_ms": kmean, "bin_iterations_per_launch": bins,
             "peak_basis": f"derived: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {sms} SMs x {f_max:.0f} MHz",
