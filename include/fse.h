@@ -261,7 +261,10 @@ int fse_extrapolate_batch(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, 
  * fse_extrapolate_host -- as fse_extrapolate_batch, but image/mask/out/out_f32
  * are HOST pointers: inputs are copied to the arena, outputs copied back, and
  * the call returns after the copies finished.  Pinned host memory makes the
- * copies asynchronous DMA.
+ * copies asynchronous DMA.  Jobs whose host rows are packed (pitch == W) move
+ * as whole planes; where the device rows need padding to 16 bytes a device
+ * kernel re-pitches them (inputs) and packs them again (outputs).  Strided
+ * host rows (pitch > W) are copied row by row, which is slower.
  */
 int fse_extrapolate_host(fse_context_t* ctx, const fse_job_t* jobs, int32_t n, void* cuda_stream,
                          fse_stats_t* stats);

@@ -209,21 +209,66 @@ int enqueue_host(Context* c, const fse_job_t* jobs, int32_t n, cudaStream_t st,
   }
   off = (off + 255) / 256 * 256;
   if (off >= c->arena_bytes) return fail(FSE_ENOMEM, "arena too small for the host path");
+  // Copies move whole contiguous planes (a strided copy of short rows runs far
+  // below the link's bandwidth): a job whose host rows are packed (pitch = W)
+  // but whose device rows are padded goes through a packed area and a re-pitch
+  // kernel.  The packed area lies where the call's plan will be built: the
+  // re-pitch runs before the plan is uploaded, and the outputs are packed there
+  // after the last kernel that reads the plan, all in stream order.
+  size_t packed = 0;
+  for (int i = 0; i < n; ++i)
+    if (jobs[i].pitch == jobs[i].W && dj[i].pitch != jobs[i].W) packed += 2 * (size_t)jobs[i].W * jobs[i].H;
+  // (not with debug capture, whose records live in the plan region and are read after the call)
+  const bool use_packed = !c->debug && off + packed + 256 * (size_t)n <= c->arena_bytes;
+  std::vector<size_t> pk(n, 0);
+  {
+    size_t o = off;
+    for (int i = 0; i < n; ++i) {
+      pk[i] = o;
+      if (jobs[i].pitch == jobs[i].W && dj[i].pitch != jobs[i].W)
+        o = (o + 2 * (size_t)jobs[i].W * jobs[i].H + 255) / 256 * 256;
+    }
+  }
   for (int i = 0; i < n; ++i) {
     const fse_job_t& j = jobs[i];
-    cudaError_t e = cudaMemcpy2DAsync((void*)dj[i].image, dj[i].pitch, j.image, j.pitch, j.W, j.H,
-                                      cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync((void*)dj[i].mask, dj[i].pitch, j.mask, j.pitch, j.W, j.H,
+    const size_t px = (size_t)j.W * j.H;
+    cudaError_t e;
+    if (j.pitch == j.W && dj[i].pitch == j.W) {  // both packed: plain copies
+      e = cudaMemcpyAsync((void*)dj[i].image, j.image, px, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync((void*)dj[i].mask, j.mask, px, cudaMemcpyHostToDevice, st);
+    } else if (j.pitch == j.W && use_packed) {
+      // image then mask into the packed area, one re-pitch for both planes
+      // (the device mask follows the image at a fixed distance)
+      char* p = c->arena + pk[i];
+      e = cudaMemcpyAsync(p, j.image, px, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(p + px, j.mask, px, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = launch_repitch((const uint8_t*)p, j.W, px, (uint8_t*)dj[i].image, dj[i].pitch,
+                           (size_t)((const char*)dj[i].mask - (const char*)dj[i].image), j.W, j.H, 2, st);
+    } else {
+      e = cudaMemcpy2DAsync((void*)dj[i].image, dj[i].pitch, j.image, j.pitch, j.W, j.H,
                             cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync((void*)dj[i].mask, dj[i].pitch, j.mask, j.pitch, j.W, j.H,
+                              cudaMemcpyHostToDevice, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
   }
   int rc = run_batch(c, dj.data(), n, st, stats, off);
   if (rc) return rc;
   for (int i = 0; i < n; ++i) {
     const fse_job_t& j = jobs[i];
-    cudaError_t e = cudaMemcpy2DAsync(j.out, j.pitch, dj[i].out, dj[i].pitch, j.W, j.H,
-                                      cudaMemcpyDeviceToHost, st);
+    const size_t px = (size_t)j.W * j.H;
+    cudaError_t e;
+    if (j.pitch == j.W && dj[i].pitch == j.W) {
+      e = cudaMemcpyAsync(j.out, dj[i].out, px, cudaMemcpyDeviceToHost, st);
+    } else if (j.pitch == j.W && use_packed) {
+      char* p = c->arena + pk[i];
+      e = launch_repitch(dj[i].out, dj[i].pitch, 0, (uint8_t*)p, j.W, 0, j.W, j.H, 1, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(j.out, p, px, cudaMemcpyDeviceToHost, st);
+    } else {
+      e = cudaMemcpy2DAsync(j.out, j.pitch, dj[i].out, dj[i].pitch, j.W, j.H, cudaMemcpyDeviceToHost, st);
+    }
     if (e == cudaSuccess && j.out_f32)
       e = cudaMemcpyAsync(j.out_f32, dj[i].out_f32, sizeof(float) * j.W * j.H,
                           cudaMemcpyDeviceToHost, st);

@@ -164,6 +164,8 @@ cudaError_t launch_mark(const ExecArgs& a, int n_tiles, int max_tile_blocks, cud
 cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st);
 cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st, const ExecCfg& cfg);
 cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st);
+cudaError_t launch_repitch(const uint8_t* src, int src_pitch, size_t src_plane, uint8_t* dst, int dst_pitch,
+                           size_t dst_plane, int W, int H, int planes, cudaStream_t st);
 bool exec_cfg_valid(int cls, int layout, int unroll);  // a kernel variant exists
 int exec_threads(int cls, const ExecCfg& cfg);
 size_t exec_smem(int cls, const ExecCfg& cfg);

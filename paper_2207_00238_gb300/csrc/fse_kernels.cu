@@ -25,6 +25,7 @@
 // with an error flag that the host reads; nothing traps.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <type_traits>
@@ -2290,6 +2291,28 @@ cudaError_t launch_exec(const ExecArgs& a, int cls, int grid, cudaStream_t st, c
 
 cudaError_t launch_probe(const ExecArgs& a, cudaStream_t st) {
   k_probe<<<1, 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Row re-pitch of `planes` byte planes of W x H (host-buffer path): the host
+// copies move whole contiguous planes, this kernel moves rows between the
+// packed and the 16-byte-padded layouts.
+__global__ void k_repitch(const uint8_t* __restrict__ src, int src_pitch, size_t src_plane,
+                          uint8_t* __restrict__ dst, int dst_pitch, size_t dst_plane, int W, int H) {
+  const uint8_t* s = src + blockIdx.y * src_plane;
+  uint8_t* d = dst + blockIdx.y * dst_plane;
+  for (int y = blockIdx.x; y < H; y += gridDim.x) {
+    const uint8_t* sr = s + (size_t)y * src_pitch;
+    uint8_t* dr = d + (size_t)y * dst_pitch;
+    for (int x = threadIdx.x; x < W; x += blockDim.x) dr[x] = sr[x];
+  }
+}
+
+cudaError_t launch_repitch(const uint8_t* src, int src_pitch, size_t src_plane, uint8_t* dst, int dst_pitch,
+                           size_t dst_plane, int W, int H, int planes, cudaStream_t st) {
+  if (W <= 0 || H <= 0 || planes <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min(H, 2048), (unsigned)planes);
+  k_repitch<<<grid, 256, 0, st>>>(src, src_pitch, src_plane, dst, dst_pitch, dst_plane, W, H);
   return cudaGetLastError();
 }
 

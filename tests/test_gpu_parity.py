@@ -279,12 +279,33 @@ def test_batch_equals_alone(ctx):
 
 
 def test_host_path_equals_device_path(ctx):
-    job = _small_tiled()
-    dev, _ = run_gpu(ctx, [job])
-    out = np.zeros_like(job["image"])
-    g = np.zeros(job["image"].shape, np.float32)
-    ctx.extrapolate_host([fse.make_job(job["image"], job["mask"], out, job["params"], out_f32=g)])
-    assert (out == dev[0]["out"]).all() and (g == dev[0]["g"]).all()
+    """The host-buffer entry point: rows that are a multiple of 16 bytes
+    (plain copies), packed rows of other widths (packed copies and a device
+    re-pitch both ways) and strided host rows (2-D copies) in one call."""
+    jobs = [_small_tiled(), _small_tiled(W=70, H=50, n_tiles=1), _small_tiled(W=53, H=41, n_tiles=2)]
+    dev, _ = run_gpu(ctx, jobs)
+    hj, outs, gs = [], [], []
+    for i, job in enumerate(jobs):
+        img, msk = job["image"], job["mask"]
+        H, W = img.shape
+        if i == 2:  # strided host rows: views into wider arrays, pitch W + 11
+            wide = [np.zeros((H, W + 11), np.uint8) for _ in range(3)]
+            wide[0][:, :W] = img
+            wide[1][:, :W] = msk
+            img, msk, out = (w[:, :W] for w in wide)
+        else:
+            out = np.zeros_like(img)
+        g = np.zeros((H, W), np.float32)
+        hj.append(fse.make_job(img, msk, out, job["params"], out_f32=g))
+        outs.append(out)
+        gs.append(g)
+    for call in range(2):  # twice: the second call reuses the packed area
+        for o, g in zip(outs, gs):
+            o[...] = 0
+            g[...] = 0
+        ctx.extrapolate_host(hj)
+        for o, g, d in zip(outs, gs, dev):
+            assert (o == d["out"]).all() and (g == d["g"]).all(), call
 
 
 def test_graph_replay(ctx):
