@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--no-tma", action="store_true", help="stage supports with plain loads")
     ap.add_argument("--no-graph", action="store_true", help="time direct launches instead of graph replay")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--root-window", type=int, default=-1,
+                    help="FSE_OPT_ROOT_WINDOW (-1: library default)")
     ap.add_argument("--class-launch", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="FSE_OPT_CLASS_LAUNCH (-1: library default / autotuned)")
     ap.add_argument("--study", default=None, choices=[None, "overlap", "tiling"],
@@ -537,6 +539,8 @@ def main():
         ctx.set_option(fse.OPT_CTAS_PER_SM, args.ctas_per_sm)
     if args.class_launch >= 0:
         ctx.set_option(fse.OPT_CLASS_LAUNCH, args.class_launch)
+    if args.root_window >= 0:
+        ctx.set_option(fse.OPT_ROOT_WINDOW, args.root_window)
     keep, cjobs, pix = [], [], 0
     for j in jobs:
         img = torch.from_numpy(j["image"]).to(dev)

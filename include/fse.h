@@ -200,6 +200,14 @@ void fse_context_destroy(fse_context_t* ctx);
                                    1 (default) = concurrently on forked streams,
                                    the F = 64 class first; 2 = concurrently,
                                    the F = 32 class first                      */
+#define FSE_OPT_ROOT_WINDOW 15  /* batch calls (DAG mode): blocks without lost
+                                   predecessors enter the ready queue as a
+                                   window of n per consumer (a warp of the F = 32
+                                   executor, a CTA of the others), one more
+                                   whenever a block finishes, in job order, so
+                                   a few images at a time are in flight and
+                                   their supports stay in L2; 0 = all at once.
+                                   Results do not depend on it.  Default 2.    */
 #define FSE_EXEC_DAG 0       /* one persistent launch per work class, the classes
                                 concurrent (FSE_OPT_CLASS_LAUNCH); blocks start
                                 as soon as the blocks they depend on are done  */

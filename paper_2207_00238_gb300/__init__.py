@@ -22,6 +22,7 @@ TILING = {"alg1": 0, "vertical": 1}
 OPT_EXEC_MODE, OPT_TIMEOUT_MS, OPT_CTAS_PER_SM, OPT_USE_GRAPH, OPT_DEBUG_CAPTURE, OPT_KERNEL_TIMING = 1, 2, 3, 4, 5, 6
 OPT_F64_WARPS, OPT_F32_LAYOUT, OPT_TMA_STAGING, OPT_DEBUG_TMA_STALL = 7, 8, 9, 10
 OPT_F32_UNROLL, OPT_F64_UNROLL, OPT_CLASS_LAUNCH, OPT_SERVER_CLASSES = 11, 12, 13, 14
+OPT_ROOT_WINDOW = 15
 EXEC = {"dag": 0, "levels": 1, "per_block": 2}
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 

@@ -334,6 +334,7 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
     case FSE_OPT_CTAS_PER_SM:
       if (value < 0 || value > 64) return fse::fail(FSE_EINVAL, "ctas_per_sm");
       c->ctas_per_sm = (int)value;
+      c->graph_jobs.clear();  // the grid (and the root window) of a captured graph
       return FSE_OK;
     case FSE_OPT_USE_GRAPH:
       c->use_graph = value != 0;
@@ -375,6 +376,11 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
     case FSE_OPT_SERVER_CLASSES:
       if (value < 1 || value > 3) return fse::fail(FSE_EINVAL, "server classes %d", (int)value);
       c->server_classes = (int)value;
+      return FSE_OK;
+    case FSE_OPT_ROOT_WINDOW:
+      if (value < 0 || value > 64) return fse::fail(FSE_EINVAL, "root window %d", (int)value);
+      c->root_window = (int)value;
+      c->graph_jobs.clear();
       return FSE_OK;
     case FSE_OPT_CLASS_LAUNCH:
       if (value < 0 || value > 2) return fse::fail(FSE_EINVAL, "class launch %d", (int)value);

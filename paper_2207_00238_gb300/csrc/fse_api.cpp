@@ -324,7 +324,7 @@ struct Plan {
   int K_max = 0;
   int64_t pixels = 0;
   // arena offsets (bytes)
-  size_t o_jobs, o_tiles, o_wf, o_wd, o_map, o_items[MAX_CLS], o_cnt[MAX_CLS], o_slots[MAX_CLS],
+  size_t o_jobs, o_tiles, o_wf, o_wd, o_map, o_items[MAX_CLS], o_cnt[MAX_CLS], o_slots[MAX_CLS], o_roots[MAX_CLS], o_tcnt, o_tctr, o_tbase,
       o_valf, o_vald, o_q, o_level, o_dbg_rec, o_dbg_useq, o_tmap, upload_bytes, ff_begin, ff_end,
       zero_begin, zero_end, total;
 };
@@ -436,6 +436,8 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
   for (int k = 0; k < MAX_CLS; ++k) {
     P.o_items[k] = take(sizeof(int2) * P.cap[k]);
     P.o_cnt[k] = take(sizeof(int32_t) * P.cap[k]);
+    P.o_roots[k] = take(sizeof(int32_t) * P.cap[k]);
+    if (k == 0) P.o_tbase = take(sizeof(int32_t) * std::max<size_t>(1, P.tiles.size()));
   }
   int64_t capmax = std::max({P.cap[0], P.cap[1], P.cap[2]});
   P.o_level = take(c->exec_mode == FSE_EXEC_DAG ? 0 : sizeof(int32_t) * MAX_CLS * capmax);
@@ -450,6 +452,8 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
   o = P.ff_end;
   P.zero_begin = o;
   P.o_q = take(sizeof(QueueDev) * MAX_CLS);
+  P.o_tcnt = take(sizeof(int32_t) * std::max<size_t>(1, P.tiles.size()));
+  P.o_tctr = take(sizeof(int32_t) * std::max<size_t>(1, P.tiles.size()));
   P.zero_end = align_up(o, 256);
   o = P.zero_end;
   P.o_dbg_useq = take(c->debug ? sizeof(int32_t) * KMAX * MAX_CLS * capmax : 0);
@@ -496,6 +500,18 @@ static ExecArgs make_args(Context* c, const Plan& P) {
     a.c[k].items = reinterpret_cast<int2*>(base + P.o_items[k]);
     a.c[k].cnt = reinterpret_cast<int32_t*>(base + P.o_cnt[k]);
     a.c[k].slots = reinterpret_cast<int32_t*>(base + P.o_slots[k]);
+    a.c[k].roots = reinterpret_cast<int32_t*>(base + P.o_roots[k]);
+    if (k == 0) {  // ordered enumeration: each tile's items one contiguous id range
+      a.tile_cnt = reinterpret_cast<int32_t*>(base + P.o_tcnt);
+      a.tile_ctr = reinterpret_cast<int32_t*>(base + P.o_tctr);
+      a.tile_base = reinterpret_cast<int32_t*>(base + P.o_tbase);
+      a.n_tiles = (int32_t)P.tiles.size();
+    }
+    // fed roots in DAG mode: a window of root_window items per consumer
+    // (a warp of the F = 32 executor, a CTA of the others)
+    a.c[k].window = c->exec_mode == FSE_EXEC_DAG && c->root_window > 0
+                        ? c->root_window * exec_grid(c, k) * (k == CLS_F32_32 ? exec_threads(k, c->cfg) / 32 : 1)
+                        : 0;
     a.c[k].q = reinterpret_cast<QueueDev*>(base + P.o_q) + k;
     a.c[k].cap = (int32_t)P.cap[k];
   }
@@ -535,7 +551,7 @@ static int enqueue(Context* c, const Plan& P, const ExecArgs& a, cudaStream_t st
     FSE_CUDA(cudaMemsetAsync(c->arena + P.o_dbg_useq, 0xFF, P.total - P.o_dbg_useq, st));
   FSE_CUDA(launch_init_out(a.jobs, (int)P.jobs.size(), P.max_pixels, st));
   FSE_CUDA(launch_mark(a, (int)P.tiles.size(), P.max_tile_blocks, st));
-  launches += 2;
+  launches += P.tiles.empty() ? 1 : 4;  // init_out; mark: count, scan, assign
   for (int k = 0; k < MAX_CLS; ++k)
     if (P.cap[k] > 0) {
       FSE_CUDA(launch_deps(a, k, (int)P.cap[k], st));

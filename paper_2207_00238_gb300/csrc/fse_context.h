@@ -41,6 +41,7 @@ struct fse_context {
   int capturing = 0;
   int dbg_tma_stall = 0;  // test only (FSE_OPT_DEBUG_TMA_STALL)
   int server_classes = 3;  // FSE_OPT_SERVER_CLASSES of servers made from this context
+  int root_window = 2;     // FSE_OPT_ROOT_WINDOW: fed roots per consumer (0 = all at once)
   std::vector<cudaEvent_t> tev;  // pairs: start, end of the iteration kernels
   size_t tev_used = 0;
   fse::ExecCfg cfg;                    // executor variant per class (options, autotuner)

@@ -71,6 +71,9 @@ struct QueueDev {
   int32_t n_core;   // lost blocks that touch their tile's core
   int32_t error;    // ErrBits
   int32_t error_info;
+  int32_t n_roots;    // items without lost predecessors (fed roots, see ClassArgs::window)
+  int32_t root_next;  // roots fed by finished blocks so far
+  int32_t pad_[2];
 };
 
 struct ClassArgs {
@@ -79,7 +82,17 @@ struct ClassArgs {
   int32_t* slots;   // ready queue, -1 = not yet pushed
   QueueDev* q;
   int32_t cap;
+  // Fed roots (batch calls, DAG mode): the first `window` items without lost
+  // predecessors start in the queue, the others wait in `roots` (id order) and
+  // a finished block pushes the next ones only while fewer than `window` items
+  // wait, so released successors go first and the queue follows a few images
+  // at a time (their supports stay in L2) instead of sweeping every processing
+  // phase across the whole batch.  0 = every root at once.
+  int32_t* roots;
+  int32_t window;
 };
+
+constexpr int NW32 = 2;  // F = 32 executor: warps (independent workers) per CTA
 
 // Continuous-batching server state (fse_server.cpp).  Work items of every
 // resident request share one queue per class that lives as long as the
@@ -141,6 +154,13 @@ struct ExecArgs {
   ServerHostCtl* host;  // device address of the host-mapped control block
   int32_t* level_of;    // per class item level (levels mode), class stride level_stride
   int64_t level_stride;
+  // ordered enumeration (batch calls): per tile lost-block count, first item
+  // id and assignment counter, so each tile's items get one contiguous id
+  // range in tile (= job) order; null = ids in arrival order (one pass)
+  int32_t* tile_cnt;
+  int32_t* tile_base;
+  int32_t* tile_ctr;
+  int32_t n_tiles;
 };
 
 // Executor configuration of one context: which kernel variant runs each work

@@ -162,10 +162,27 @@ __device__ __forceinline__ int count_preds(const JobDev& J, const TileDev& T, co
   return cnt;
 }
 
+// Fed roots (ClassArgs::window): while fewer than `window` items wait in the
+// queue, a finished block pushes the next root (four when consumers are
+// already waiting), so released successors keep the queue filled and new
+// roots, in id (job) order, enter only as the queue runs low.
+__device__ __forceinline__ void feed_root(const ClassArgs& C) {
+  const int pending = ld_relaxed(&C.q->tail) - ld_relaxed(&C.q->head);
+  const int n = pending < 0 ? 4 : (pending < C.window ? 1 : 0);
+  const int n_roots = ld_relaxed(&C.q->n_roots);
+  for (int i = 0; i < n; ++i) {
+    const int idx = C.window + atomicAdd(&C.q->root_next, 1);
+    if (idx >= n_roots) break;
+    queue_push(C, __ldcg(C.roots + idx));
+  }
+}
+
 // After a block's writes are globally visible: decrement the pending count
-// of every later lost block in its dependency window, queue those reaching 0.
+// of every later lost block in its dependency window, queue those reaching 0;
+// with fed roots, also queue the next root.
 __device__ __forceinline__ void release_successors(const ExecArgs& a, const ClassArgs& C, const TileDev& T,
                                    const JobDev& J, int I, int Jb, int t, int nthr) {
+  if (C.window > 0 && t == 0 && !a.level_mode && a.single_item < 0) feed_root(C);
   if (J.order == ORDER_INDEPENDENT || a.level_mode || a.single_item >= 0) return;
   const int D = J.D, wd = 2 * D + 1;
   const int64_t kx = order_key(J, I, Jb);
@@ -985,7 +1002,6 @@ struct alignas(128) WarpSmem32 {
   TileDev T;              // descriptors of the current block's tile and job
   JobDev J;
 };
-constexpr int NW32 = 2;  // warps (independent workers) per CTA
 constexpr size_t SMEM32 = 64 * sizeof(float2) + NW32 * sizeof(WarpSmem32);
 
 // Prologue of one F = 32 block: descriptors into shared memory, the support
@@ -2180,19 +2196,139 @@ __global__ void k_mark(const __grid_constant__ ExecArgs a) {
 }
 
 // Pending-predecessor count of every item; items without any are queued.
+// Ordered enumeration, pass 1: mark the lost blocks of every tile (map -2,
+// or -3 when the block touches the core) and count them per tile.
+__device__ __forceinline__ void lost_test(const TileDev& T, const JobDev& J, int I, int Jb, bool& lost, bool& core) {
+  lost = false;
+  core = false;
+  const int y0 = I * J.b, x0 = Jb * J.b;
+  for (int yy = y0; yy < min(y0 + J.b, T.eh); ++yy)
+    for (int xx = x0; xx < min(x0 + J.b, T.ew); ++xx) {
+      const int gy = T.ey + yy, gx = T.ex + xx;
+      if (J.mask[(size_t)gy * J.pitch + gx]) {
+        lost = true;
+        if (gx >= T.x && gx < T.x + T.w && gy >= T.y && gy < T.y + T.h) core = true;
+      }
+    }
+}
+
+__global__ void k_mark_count(const __grid_constant__ ExecArgs a) {
+  const TileDev T = a.tiles[blockIdx.y];
+  const JobDev J = a.jobs[T.job];
+  const int nb = T.nbx * T.nby;
+  const ClassArgs& C = a.c[T.cls];
+  const int lane = threadIdx.x & 31;
+  for (int k0 = blockIdx.x * blockDim.x; k0 < nb; k0 += gridDim.x * blockDim.x) {  // uniform per warp
+    const int k = k0 + threadIdx.x;
+    bool lost = false, core = false;
+    if (k < nb) {
+      lost_test(T, J, k / T.nbx, k % T.nbx, lost, core);
+      a.map[T.map_off + k] = lost ? (core ? -3 : -2) : -1;
+    }
+    const unsigned bl = __ballot_sync(0xffffffffu, lost), bc = __ballot_sync(0xffffffffu, core);
+    if (lane == 0 && bl) atomicAdd(&a.tile_cnt[blockIdx.y], __popc(bl));
+    if (lane == 0 && bc) atomicAdd(&C.q->n_core, __popc(bc));
+  }
+}
+
+// Pass 2 (one block): per class, the first item id of every tile, tiles in
+// order; the class's item count.
+__global__ void k_mark_scan(const __grid_constant__ ExecArgs a) {
+  __shared__ int wsum[32];
+  __shared__ int carry[MAX_CLS];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+  if (t < MAX_CLS) carry[t] = 0;
+  __syncthreads();
+  for (int t0 = 0; t0 < a.n_tiles; t0 += blockDim.x) {
+    const int i = t0 + t;
+    const int cls = i < a.n_tiles ? a.tiles[i].cls : -1;
+    const int cnt = i < a.n_tiles ? a.tile_cnt[i] : 0;
+    for (int k = 0; k < MAX_CLS; ++k) {
+      const int v = cls == k ? cnt : 0;
+      int x = v;  // inclusive warp scan
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) wsum[w] = x;
+      __syncthreads();
+      int before = 0;
+      for (int q = 0; q < w; ++q) before += wsum[q];
+      if (cls == k) a.tile_base[i] = carry[k] + before + x - v;
+      __syncthreads();
+      if (t == 0) {
+        int tot = 0;
+        for (int q = 0; q < nw; ++q) tot += wsum[q];
+        carry[k] += tot;
+      }
+      __syncthreads();
+    }
+  }
+  if (t < MAX_CLS) {
+    QueueDev* q = a.c[t].q;
+    q->n_items = carry[t];
+    if (carry[t] > a.c[t].cap) atomicOr(&q->error, ERR_BOUNDS);
+  }
+}
+
+// Pass 3: ids within each tile's range (a warp's lost blocks consecutive).
+__global__ void k_mark_assign(const __grid_constant__ ExecArgs a) {
+  const TileDev T = a.tiles[blockIdx.y];
+  const int nb = T.nbx * T.nby;
+  const ClassArgs& C = a.c[T.cls];
+  const int lane = threadIdx.x & 31;
+  for (int k0 = blockIdx.x * blockDim.x; k0 < nb; k0 += gridDim.x * blockDim.x) {  // uniform per warp
+    const int k = k0 + threadIdx.x;
+    const int m = k < nb ? a.map[T.map_off + k] : -1;
+    const bool lost = m <= -2;
+    const unsigned bl = __ballot_sync(0xffffffffu, lost);
+    int base = 0;
+    if (lane == 0 && bl) base = atomicAdd(&a.tile_ctr[blockIdx.y], __popc(bl));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lost) {
+      const int id = a.tile_base[blockIdx.y] + base + __popc(bl & ((1u << lane) - 1u));
+      if (id < C.cap) {
+        C.items[id] = make_int2(blockIdx.y, ((k / T.nbx) << 16) | (k % T.nbx));
+        a.map[T.map_off + k] = id;
+      } else {
+        a.map[T.map_off + k] = -1;
+      }
+    }
+  }
+}
+
 __global__ void k_deps(const __grid_constant__ ExecArgs a, int cls) {
   const ClassArgs& C = a.c[cls];
   const int n = min(C.q->n_items, C.cap);
-  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
-    const int2 it = ld_in(C.items + id, a.server != 0);
-    const TileDev T = a.tiles[it.x];
-    const JobDev J = a.jobs[T.job];
-    const int I = it.y >> 16, Jb = it.y & 0xFFFF;
-    const int cnt = count_preds(J, T, a.map + T.map_off, I, Jb, false);
-    C.cnt[id] = cnt;
-    if (a.level_of) a.level_of[(size_t)cls * a.level_stride + id] =
-        J.order == ORDER_PHASED ? (I % J.P) * J.P + (Jb % J.P) : 0;
-    if (cnt == 0) queue_push(C, id);
+  const int lane = threadIdx.x & 31;
+  for (int id0 = blockIdx.x * blockDim.x; id0 < n; id0 += gridDim.x * blockDim.x) {  // uniform per warp
+    const int id = id0 + threadIdx.x;
+    int cnt = -1;
+    if (id < n) {
+      const int2 it = ld_in(C.items + id, a.server != 0);
+      const TileDev T = a.tiles[it.x];
+      const JobDev J = a.jobs[T.job];
+      const int I = it.y >> 16, Jb = it.y & 0xFFFF;
+      cnt = count_preds(J, T, a.map + T.map_off, I, Jb, false);
+      C.cnt[id] = cnt;
+      if (a.level_of) a.level_of[(size_t)cls * a.level_stride + id] =
+          J.order == ORDER_PHASED ? (I % J.P) * J.P + (Jb % J.P) : 0;
+    }
+    if (C.window > 0) {
+      // fed roots: a warp's roots take consecutive places in id order; the
+      // first `window` start, the others wait
+      const unsigned br = __ballot_sync(0xffffffffu, cnt == 0);
+      int base = 0;
+      if (lane == 0 && br) base = atomicAdd(&C.q->n_roots, __popc(br));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (cnt == 0) {
+        const int r = base + __popc(br & ((1u << lane) - 1u));
+        if (r < C.window) queue_push(C, id);
+        else C.roots[r] = id;
+      }
+    } else if (cnt == 0) {
+      queue_push(C, id);
+    }
   }
 }
 
@@ -2272,13 +2408,30 @@ cudaError_t launch_init_out(const JobDev* jobs_dev, int n_jobs, int max_pixels, 
 cudaError_t launch_mark(const ExecArgs& a, int n_tiles, int max_tile_blocks, cudaStream_t st) {
   if (n_tiles == 0) return cudaSuccess;
   dim3 grid((unsigned)std::min(4096, (max_tile_blocks + 255) / 256 + 1), (unsigned)n_tiles);
-  k_mark<<<grid, 256, 0, st>>>(a);
+  if (!a.tile_cnt) {
+    k_mark<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  k_mark_count<<<grid, 256, 0, st>>>(a);
+  k_mark_scan<<<1, 1024, 0, st>>>(a);
+  k_mark_assign<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+static int sm_count_of_device() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    return 132;
+  return n;
 }
 
 cudaError_t launch_deps(const ExecArgs& a, int cls, int cap, cudaStream_t st) {
   if (cap == 0) return cudaSuccess;
-  k_deps<<<(unsigned)std::min(8192, (cap + 255) / 256), 256, 0, st>>>(a, cls);
+  // with fed roots a grid of one wave keeps the roots close to id order
+  const int blocks = a.c[cls].window > 0 ? std::min(sm_count_of_device() * 8, (cap + 255) / 256)
+                                         : std::min(8192, (cap + 255) / 256);
+  k_deps<<<(unsigned)std::max(1, blocks), 256, 0, st>>>(a, cls);
   return cudaGetLastError();
 }
 

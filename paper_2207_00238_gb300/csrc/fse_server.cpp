@@ -128,6 +128,7 @@ struct fse_server {
   int64_t hb_timeout_ns = 0;
   char* arena = nullptr;
   size_t arena_bytes = 0;
+  size_t pool_capacity = 0;  // bytes of the request pool
   // arena layout
   fse::ServerDevCtl* dctl = nullptr;
   fse::QueueDev* dq = nullptr;
@@ -663,6 +664,7 @@ int fse_server_create(fse_server_t** out, fse_context_t* ctx, const fse_server_c
     s->slots[k] = reinterpret_cast<int32_t*>(s->arena + take(sizeof(int32_t) * s->cap));
   }
   s->pool.reset(align256(o), s->arena_bytes);
+  s->pool_capacity = s->arena_bytes > align256(o) ? s->arena_bytes - align256(o) : 0;
   s->staging_bytes = (size_t)256 << 20;
   cudaError_t e = cudaMallocHost(&s->mirror, sizeof(fse::ServerDevCtl));
   if (e == cudaSuccess) e = cudaHostAlloc(&s->hctl, sizeof(fse::ServerHostCtl), cudaHostAllocMapped);
@@ -717,11 +719,13 @@ int fse_submit(fse_server_t* s, const fse_job_t* job, uint64_t* ticket) {
   r->cls = cls;
   r->dev_bytes = request_bytes(*job, r->tiles, &r->block_bound);
   const size_t px = (size_t)job->W * job->H;
-  if (r->dev_bytes > s->pool.largest() || r->block_bound + 1 + s->consumers[cls] > s->cap ||
+  // against the pool's capacity: a request that fits waits in the queue until
+  // memory frees up (the free map itself belongs to the worker thread)
+  if (r->dev_bytes > s->pool_capacity || r->block_bound + 1 + s->consumers[cls] > s->cap ||
       align256(px) * 2 + 65536 > s->staging_bytes || align256(px) * 5 > s->staging_bytes)
     return fse::fail(FSE_ENOMEM, "request needs %zu device bytes and %lld queue entries; the server has "
-                                 "%zu bytes free and %lld entries", r->dev_bytes, (long long)r->block_bound,
-                     s->pool.largest(), (long long)s->cap);
+                                 "%zu bytes of request memory and %lld entries", r->dev_bytes, (long long)r->block_bound,
+                     s->pool_capacity, (long long)s->cap);
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return fse::fail(FSE_ECANCELLED, "server shutting down");

@@ -278,6 +278,31 @@ def test_batch_equals_alone(ctx):
         assert (alone[0]["out"] == m["out"]).all() and (alone[0]["g"] == m["g"]).all()
 
 
+def test_root_window_does_not_change_results(ctx):
+    """Fed roots (FSE_OPT_ROOT_WINDOW) only change when blocks without lost
+    predecessors enter the queue; every block still waits for its
+    predecessors, so outputs and model values are bitwise those of the
+    all-at-once queue, for windows down to one root per consumer."""
+    # one CTA per SM keeps the window (roots per consumer x consumers) below
+    # the number of roots, so most roots are fed by finished blocks
+    jobs = [_defects(W=400, H=300), _small_tiled(W=512, H=384, n_tiles=4), synth.plain_64()[0],
+            _small_tiled(W=70, H=50, n_tiles=1)]
+    jobs += [dict(j, params=dict(j["params"], order="raster")) for j in (_defects(W=80, H=64), _small_tiled(W=96))]
+    ctx.set_option(fse.OPT_CTAS_PER_SM, 1)
+    ctx.set_option(fse.OPT_ROOT_WINDOW, 0)
+    try:
+        ref, st0 = run_gpu(ctx, jobs)
+        for w in (1, 2, 5):
+            ctx.set_option(fse.OPT_ROOT_WINDOW, w)
+            got, st = run_gpu(ctx, jobs)
+            assert st["lost_blocks"] == st0["lost_blocks"]
+            for r, g in zip(ref, got):
+                assert (r["out"] == g["out"]).all() and (r["g"] == g["g"]).all(), w
+    finally:
+        ctx.set_option(fse.OPT_ROOT_WINDOW, 2)
+        ctx.set_option(fse.OPT_CTAS_PER_SM, 0)
+
+
 def test_host_path_equals_device_path(ctx):
     """The host-buffer entry point: rows that are a multiple of 16 bytes
     (plain copies), packed rows of other widths (packed copies and a device
