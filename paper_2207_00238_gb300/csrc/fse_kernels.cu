@@ -1677,15 +1677,15 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
   // keys are resolved by the lowest flat index (lane ballot, then warps)
   const uint32_t kmask = opaque(~(uint32_t)(RPT - 1));
 
-  uint32_t bq[4] = {0u, 0u, 0u, 0u};
+  uint32_t bq[2] = {0u, 0u};
   static_for<0, RPT / 2>([&](auto h) {
     constexpr int i = 2 * decltype(h)::value;
     const float e0 = fmaf(R[i].y, R[i].y, R[i].x * R[i].x);
     const float e1 = fmaf(R[i + 1].y, R[i + 1].y, R[i + 1].x * R[i + 1].x);
-    bq[(i >> 1) & 3] = max3u(bq[(i >> 1) & 3], make_key<(uint32_t)(RPT - 1 - i)>(e0, kmask),
+    bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i)>(e0, kmask),
                              make_key<(uint32_t)(RPT - 2 - i)>(e1, kmask));
   });
-  uint32_t best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
+  uint32_t best = max(bq[0], bq[1]);
   for (int iter = 0; iter < K; ++iter) {
     {
       const uint32_t wbest = __reduce_max_sync(0xffffffffu, best);
@@ -1717,7 +1717,7 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
     const float2* wp =
         sm.Wd + (ROWS == 128 ? r0 + 64 : (r0 < 0 ? r0 + 64 : r0)) * 64 + ((c - u2) & 63);
     const float ndx = -dx, ndy = -dy;
-    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
+    bq[0] = bq[1] = 0u;
     static_for<0, RPT / 2>([&](auto h) {
       constexpr int i = 2 * decltype(h)::value;
       float e[2];
@@ -1731,10 +1731,10 @@ __device__ __forceinline__ void item_f32_64(const ExecArgs& a, int id, CtaSmem64
         R[i + k] = make_float2(rx, ry);
         e[k] = fmaf(ry, ry, rx * rx);
       }
-      bq[(i >> 1) & 3] = max3u(bq[(i >> 1) & 3], make_key<(uint32_t)(RPT - 1 - i)>(e[0], kmask),
+      bq[(i >> 1) & 1] = max3u(bq[(i >> 1) & 1], make_key<(uint32_t)(RPT - 1 - i)>(e[0], kmask),
                                make_key<(uint32_t)(RPT - 2 - i)>(e[1], kmask));
     });
-    best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
+    best = max(bq[0], bq[1]);
   }
   __syncthreads();
   if (a.dbg_useq)
@@ -1822,15 +1822,15 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
   // thread's bin index (increasing with the flat index k1 * 64 + column);
   // equal keys are resolved by the lowest flat index (lane ballot, then warps)
   const uint32_t kmask = opaque(~31u);
-  uint32_t bq[4] = {0u, 0u, 0u, 0u};
+  uint32_t bq[2] = {0u, 0u};
   static_for<0, 16>([&](auto P) {
     constexpr int pi = decltype(P)::value;
     float2 e = __fmul2_rn(RX[pi], RX[pi]);
     e = __ffma2_rn(RY[pi], RY[pi], e);
-    bq[pi & 3] = max3u(bq[pi & 3], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+    bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
                        make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
   });
-  uint32_t best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
+  uint32_t best = max(bq[0], bq[1]);
 #pragma unroll U  // K-loop unroll factor (autotuned)
   for (int iter = 0; iter < K; ++iter) {
     {
@@ -1868,7 +1868,7 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
 #pragma unroll
     for (int m = 0; m < 4; ++m) wp[m] = Wt + ((16 * m + 4 * g - u1) & 63) * 64 + d;
     const float2 ndx2 = make_float2(-dx, -dx), dy2 = make_float2(dy, dy), ndy2 = make_float2(-dy, -dy);
-    bq[0] = bq[1] = bq[2] = bq[3] = 0u;
+    bq[0] = bq[1] = 0u;
     static_for<0, 16>([&](auto P) {
       constexpr int pi = decltype(P)::value, m = pi >> 2, j = pi & 3;
       const float4 w = wp[m][j * 64];
@@ -1881,10 +1881,10 @@ __device__ __forceinline__ void item_f32_64p(const ExecArgs& a, int id, CtaSmem6
       RY[pi] = ry;
       float2 e = __fmul2_rn(rx, rx);
       e = __ffma2_rn(ry, ry, e);
-      bq[pi & 3] = max3u(bq[pi & 3], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
+      bq[pi & 1] = max3u(bq[pi & 1], make_key<(uint32_t)(31 - 2 * pi)>(e.x, kmask),
                          make_key<(uint32_t)(30 - 2 * pi)>(e.y, kmask));
     });
-    best = max3u(bq[0], bq[1], max(bq[2], bq[3]));
+    best = max(bq[0], bq[1]);
   }
   __syncthreads();
   if (a.dbg_useq)
