@@ -278,6 +278,26 @@ def test_batch_equals_alone(ctx):
         assert (alone[0]["out"] == m["out"]).all() and (alone[0]["g"] == m["g"]).all()
 
 
+def test_item_ids_contiguous_per_tile(ctx):
+    """The ordered enumeration: within a work class, item ids follow the tile
+    (and so the job) order, each tile's lost blocks one contiguous id range."""
+    jobs = [_defects(), _small_tiled(), synth.plain_64()[0], _small_tiled(W=70, H=50, n_tiles=1),
+            _defects(W=80, H=64)]
+    ctx.set_option(fse.OPT_DEBUG_CAPTURE, 1)
+    try:
+        _, st = run_gpu(ctx, jobs)
+        rec, _ = ctx.debug_fetch(int(st["lost_blocks"]) + 8)
+    finally:
+        ctx.set_option(fse.OPT_DEBUG_CAPTURE, 0)
+    assert len(rec) == st["lost_blocks"]
+    tiles = rec[:, 1]
+    descents = int((np.diff(tiles) < 0).sum())
+    assert descents <= 2  # one non-decreasing run of tiles per work class
+    runs = tiles[np.r_[True, np.diff(tiles) != 0]]
+    assert len(runs) == len(np.unique(runs))  # no tile split over two id ranges
+    assert len({tuple(r) for r in rec}) == len(rec)
+
+
 def test_root_window_does_not_change_results(ctx):
     """Fed roots (FSE_OPT_ROOT_WINDOW) only change when blocks without lost
     predecessors enter the queue; every block still waits for its
