@@ -166,11 +166,12 @@ void fse_context_destroy(fse_context_t* ctx);
 #define FSE_OPT_F32_LAYOUT 8    /* layout of this context's F = 32 executor: 1 = one
                                    spectrum column per lane, 2 = bins paired
                                    for the two-wide FP32 instructions, 3 = one
-                                   column per lane read in row runs (35-row W
-                                   table, 6 blocks of 2 warps per SM); 4 = the
-                                   same with plain-load staging only, 8 blocks
-                                   per SM; 0 = default (3)                     */
-#define FSE_OPT_TMA_STAGING 9   /* 1 = the F = 32 executor stages each block's
+                                   column per lane read in row runs (39-row W
+                                   table, TMA staging, 6 blocks of 2 warps per
+                                   SM); 4 = the same with plain-load staging
+                                   only, 8 blocks per SM; 0 = default (4)      */
+#define FSE_OPT_TMA_STAGING 9   /* layout 3 of the F = 32 executor:
+                                   1 = it stages each block's
                                    support with TMA tensor copies where the
                                    job's image and mask are 16-byte aligned
                                    with a 16-byte multiple row pitch; 2

@@ -348,7 +348,7 @@ int fse_context_set_option(fse_context_t* c, int32_t key, int64_t value) {
       c->graph_jobs.clear();
       return FSE_OK;
     case FSE_OPT_F32_LAYOUT: {
-      const int lay = value == 0 ? 3 : (int)value;
+      const int lay = value == 0 ? 4 : (int)value;
       if (value < 0 || value > 4) return fse::fail(FSE_EINVAL, "f32 layout");
       c->cfg.lay32 = lay;
       if (!fse::exec_cfg_valid(fse::CLS_F32_32, lay, c->cfg.unroll32)) c->cfg.unroll32 = 1;

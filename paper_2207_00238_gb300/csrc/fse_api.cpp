@@ -371,7 +371,9 @@ static int build_plan(Context* c, const fse_job_t* jobs, int32_t n, size_t arena
     // in once the arena layout is known
     J.bw = (J.S + 15 + 15) & ~15;
     J.bv = (J.S + 3 + 3) & ~3;
-    J.tma = c->tma && J.cls == CLS_F32_32 && ((uintptr_t)j.image & 15) == 0 && ((uintptr_t)j.mask & 15) == 0 &&
+    // TMA staging exists in the F = 32 row-run layout 3 only
+    J.tma = c->tma && J.cls == CLS_F32_32 && c->cfg.lay32 == 3 && ((uintptr_t)j.image & 15) == 0 &&
+            ((uintptr_t)j.mask & 15) == 0 &&
             (j.pitch & 15) == 0 && J.bw <= 256 && J.S <= 256 && tmap_encoder() != nullptr;
     J.tm_mask = nullptr;
     J.tm_image = nullptr;

@@ -170,7 +170,7 @@ struct ExecArgs {
 // warps with paired bins.  unroll: K-loop unroll factor (1 or 2; 2 exists for
 // F = 32 layouts 2, 3, 4 and F = 64 layout 6).
 struct ExecCfg {
-  int32_t lay32 = 3;
+  int32_t lay32 = 4;
   int32_t lay64 = 6;
   int32_t unroll32 = 1;
   int32_t unroll64 = 1;

@@ -219,13 +219,17 @@ def test_tma_staging_dense_burst_loss(ctx):
     mask, _ = synth.block_mask(W, H, 4, int(0.45 * nb), rng)
     job = dict(image=img, mask=mask, params=synth.params(4, 14, 32, 60, n_tiles=2, overlap=16))
     res = {}
-    for tma in (0, 1):
-        ctx.set_option(fse.OPT_TMA_STAGING, tma)
-        try:
-            res[tma], st = run_gpu(ctx, [job])
-        finally:
-            ctx.set_option(fse.OPT_TMA_STAGING, 2)
-        assert st["lost_blocks"] > 5000
+    ctx.set_option(fse.OPT_F32_LAYOUT, 3)  # the row-run layout with TMA staging
+    try:
+        for tma in (0, 1):
+            ctx.set_option(fse.OPT_TMA_STAGING, tma)
+            try:
+                res[tma], st = run_gpu(ctx, [job])
+            finally:
+                ctx.set_option(fse.OPT_TMA_STAGING, 2)
+            assert st["lost_blocks"] > 5000
+    finally:
+        ctx.set_option(fse.OPT_F32_LAYOUT, 0)
     assert (res[0][0]["out"] == res[1][0]["out"]).all()
     np.testing.assert_array_equal(res[0][0]["g"], res[1][0]["g"])
 
@@ -236,6 +240,7 @@ def test_tma_wait_times_out_and_context_survives(ctx):
     context is correct."""
     job = CASES["defects_small"]()
     ref, _ = run_gpu(ctx, [job])
+    ctx.set_option(fse.OPT_F32_LAYOUT, 3)  # the row-run layout with TMA staging
     ctx.set_option(fse.OPT_TMA_STAGING, 1)
     ctx.set_option(fse.OPT_TIMEOUT_MS, 50)
     ctx.set_option(fse.OPT_DEBUG_TMA_STALL, 1)
@@ -250,6 +255,7 @@ def test_tma_wait_times_out_and_context_survives(ctx):
         got, _ = run_gpu(ctx, [job])
     finally:
         ctx.set_option(fse.OPT_TMA_STAGING, 2)
+        ctx.set_option(fse.OPT_F32_LAYOUT, 0)
     assert (got[0]["out"] == ref[0]["out"]).all()
     np.testing.assert_array_equal(got[0]["g"], ref[0]["g"])
 
