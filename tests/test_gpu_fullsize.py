@@ -230,8 +230,9 @@ def test_served_requests(ctx, oracle_lib):
                            seed=20 + k)
 
 
-@pytest.mark.xfail(strict=False, reason="FP32 spectra: a few dozen pixels per 10^5 lost pixels land 2-3 grey "
-                                        "levels from the FP64 result (near-tied late selections)")
+@pytest.mark.xfail(strict=False, reason="FP32 spectra: near-tied selections that FP32 cannot order like FP64 put "
+                                        "0-338 pixels per image 2-4 grey levels off, and on one 44 %-loss F = 64 image "
+                                        "a divergence spreads through dependent blocks (1,715 pixels, up to 28)")
 def test_fp32_max_error(ctx, oracle_lib):
     """The FP32 max-error gate (1 grey level) on every workload above; the
     1024^2 image is run here if the tests above did not run."""
