@@ -279,7 +279,7 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # serving leg: Poisson arrivals into the continuous-batching server
 # ---------------------------------------------------------------------------
-def serve_leg(fse, device, n_measured, n_warm=50, rate_hz=200.0, n_capacity=300, lookahead=48):
+def serve_leg(fse, device, n_measured, n_warm=200, rate_hz=200.0, n_capacity=300, lookahead=48):
     """The serving workload through the continuous-batching server.
 
     Poisson leg: n_warm + n_measured fresh requests (each drawn anew: size
