@@ -40,11 +40,11 @@ BYTES_PER_BIN_ITER = 8       # the gathered complex FP32 W(k-u) value
 # DRAM bytes per launch of the dominant kernel (for the 256-image batch: per
 # step, both iteration kernels) from an ncu capture of the same workload,
 # reported only while the kernel source is the one that was captured.
-CAPTURED_TRAFFIC = {"kernel_src_sha256_16": "15fd2eea41bcfe12",
-                    "tiled_1024": 8370560 + 171, "defects_4k": 58547115 + 1480789,
-                    "batch_256": 1292590048 + 280871616 + 3064203360 + 337996384}
-CAPTURED_TRAFFIC_CLASS = {"batch_256": {"k_exec_f32_64": 1292590048 + 280871616,
-                                        "k_exec_f32_32": 3064203360 + 337996384}}
+CAPTURED_TRAFFIC = {"kernel_src_sha256_16": "85c9502f29abcf82",
+                    "tiled_1024": 8358272, "defects_4k": 58633216 + 1468373,
+                    "batch_256": 1298921088 + 280961056 + 3084604128 + 338152672}
+CAPTURED_TRAFFIC_CLASS = {"batch_256": {"k_exec_f32_64": 1298921088 + 280961056,
+                                        "k_exec_f32_32": 3084604128 + 338152672}}
 
 
 def captured_traffic(workload):

@@ -232,8 +232,24 @@ __device__ int server_pop_warp(const ExecArgs& a, const ClassArgs& C, int cls, i
   int item = -1;
   if (lane == 0) {
     ServerDevCtl* d = a.srv;
-    if (ld_acquire(&d->stop)) {
-      item = -1;
+    const bool stop = ld_acquire(&d->stop) != 0;
+    if (!stop) {
+      // a posted admit command goes before the queue's items (and takes no
+      // queue slot), so a new request joins as soon as a group finishes a
+      // block, not once the queue has drained
+      const int ctail = ld_acquire(&d->cmd_tail[cls]);
+      int taken = ld_relaxed(&d->cmd_taken[cls]);
+      while (taken < ctail) {
+        const int got = atomicCAS(&d->cmd_taken[cls], taken, taken + 1);
+        if (got == taken) {
+          item = SRV_CMD_BIT | taken;
+          break;
+        }
+        taken = got;
+      }
+    }
+    if (stop || item != -1) {
+      // stopping (-1), or an admit command
     } else {
       const int pos = atomicAdd(&C.q->head, 1);
       if (pos >= C.cap) {
