@@ -461,6 +461,28 @@ def test_edge_cases(ctx, oracle_lib):
     _seq_check(oracle_lib, ctx, job)
 
 
+@pytest.mark.parametrize("block,border,fft,K,kw", [
+    (2, 15, 32, 256, {}),                          # support fills the DFT, K at its maximum
+    (16, 24, 64, 50, {}),                          # F = 64 support fills the DFT, 16x16 blocks
+    (4, 14, 32, 1, dict(gamma=1.0)),               # one iteration, full step
+    (8, 8, 32, 80, dict(rho=0.5, delta=1.0)),      # other weights, reconstructions at full weight
+    (1, 8, 32, 60, dict(order="raster")),          # single-pixel blocks, raster chains
+])
+def test_parameter_extremes(ctx, oracle_lib, block, border, fft, K, kw):
+    """Parameters at the ends of their ranges: the FP64 device path selects
+    the oracle's bins on every block and the FP32 path meets the gate."""
+    rng = synth.Rng(synth.SEED_BASE + 70 + block + K)
+    W, H = 120, 88
+    img = synth.image(W, H, rng, structure=True)
+    nb = ((W + block - 1) // block) * ((H + block - 1) // block)
+    mask, _ = synth.block_mask(W, H, block, max(1, int(0.12 * nb)), rng)
+    job = dict(image=img, mask=mask, params=synth.params(block, border, fft, K, n_tiles=2, overlap=16, **kw))
+    got, st = run_gpu(ctx, [job])
+    assert st["lost_blocks"] > 0
+    _fp32_check(oracle_lib, job, got[0])
+    _seq_check(oracle_lib, ctx, job)
+
+
 def test_invalid_jobs_rejected(ctx):
     import torch
     img = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
