@@ -483,6 +483,37 @@ def test_parameter_extremes(ctx, oracle_lib, block, border, fft, K, kw):
     _seq_check(oracle_lib, ctx, job)
 
 
+def test_contexts_keep_their_own_executor_choice(ctx):
+    """Executor variants are a context's own setting: two contexts in one
+    process, set to different variants that compute the same arithmetic (F = 32
+    column and row-run layouts, K-loop unrolled or not) and used in turn, give
+    the same bytes, and the first context's choice survives the second's."""
+    jobs = [_defects(), _small_tiled()]
+    a = fse.Context(0, arena_bytes=256 << 20)
+    b = fse.Context(0, arena_bytes=256 << 20)
+    try:
+        a.set_option(fse.OPT_F32_LAYOUT, 1)
+        a.set_option(fse.OPT_F64_WARPS, 6)
+        b.set_option(fse.OPT_F32_LAYOUT, 3)
+        b.set_option(fse.OPT_F32_UNROLL, 2)
+        b.set_option(fse.OPT_F64_WARPS, 6)
+        b.set_option(fse.OPT_F64_UNROLL, 2)
+        ra, _ = run_gpu(a, jobs)
+        rb, _ = run_gpu(b, jobs)
+        ra2, _ = run_gpu(a, jobs)  # a's choice survives b's calls
+        a.set_option(fse.OPT_KERNEL_TIMING, 1)
+        b.set_option(fse.OPT_KERNEL_TIMING, 1)
+        run_gpu(a, jobs)
+        run_gpu(b, jobs)
+        assert len(a.class_times()) == 1 and len(b.class_times()) == 1  # each records its own calls
+        for x, y, z in zip(ra, rb, ra2):
+            assert (x["out"] == y["out"]).all() and (x["g"] == y["g"]).all()
+            assert (x["out"] == z["out"]).all() and (x["g"] == z["g"]).all()
+    finally:
+        a.close()
+        b.close()
+
+
 def test_invalid_jobs_rejected(ctx):
     import torch
     img = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
